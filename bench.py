@@ -1,0 +1,337 @@
+"""Benchmark of BRMerge SpGEMM on one GB300 (or N, one independent product per GPU).
+
+Workload: C = A*A, A Erdos-Renyi with n = 2^20 rows and exactly 16 distinct
+uniform columns per row, FP64 values U[-1,1), seeded (synthetic; the paper's
+SuiteSparse matrices are not used).  One step = one whole BRMerge-Precise call
+(product counts + binning, symbolic pass, prefix sum, allocation of C,
+numeric pass) on inputs already resident in HBM.  The inputs (A: 205 MB) and
+the output (C: 3.2 GB) are both larger than the 129 MB L2, so no explicit L2
+flush is needed between steps.
+
+Metric (the paper's, Section IV-A): GFLOP/s = 2 * intermediate products / s.
+
+Printed: one JSON line with value (device-timed, all ranks), e2e (through the
+same C-ABI call with host buffers: A copied in from pinned host memory and C
+copied back every step), the roofline of the dominant kernel (the numeric
+warp-bin kernel, timed live with CUDA events recorded by the library on its
+launch stream), clocks sampled with nvidia-smi during the timed region, and a
+cpu_baseline (the CPU oracle on a bounded sample of rows).
+
+``--impl reference`` times the CPU oracle itself (the only reference that
+exists for this method) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2206_06611_gb300 import inputs as I  # noqa: E402
+
+METRIC = "SpGEMM GFLOP/s (2*products/s)"
+UNIT = "GFLOP/s"
+WORKLOAD = "ER n=2^20, 16 nnz/row, C=A*A, FP64, BRMerge-Precise"
+
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
+# capture of the current kernel source; None until captured for this version.
+NUMERIC_WARP_TRAFFIC = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index: int):
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(dev_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of the numeric pass (compulsory traffic, per launch)
+# ---------------------------------------------------------------------------
+def numeric_bytes(A, B, nnz_c, vbytes):
+    """A once (row_ptr, col, val), the B rows A touches once, C.row_ptr read
+    once and C's columns and values written once."""
+    touched = np.zeros(B.rows, dtype=bool)
+    touched[A.col] = True
+    blen = np.diff(B.rp.astype(np.int64))
+    b_bytes = int(touched.sum()) * 2 * 4 + int(blen[touched].sum()) * (4 + vbytes)
+    a_bytes = (A.rows + 1) * 4 + A.nnz * (4 + vbytes)
+    c_bytes = (A.rows + 1) * 8 + nnz_c * (4 + vbytes)
+    return a_bytes + b_bytes + c_bytes
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(A, target_s: float, threads: int):
+    """Time the oracle's Gustavson (row-parallel over nprod-balanced groups)
+    on the first rows of A*A, enough for about target_s seconds."""
+    import oracle
+    oracle.build()
+    nprod = oracle.row_nprod(A, A)
+    # calibrate on a small slice
+    rows = np.arange(min(A.rows, 20000), dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.gustavson_parallel(A, A, threads, rows)
+    dt = time.perf_counter() - t0
+    rate = nprod[rows].sum() / max(dt, 1e-6)
+    want = int(min(A.rows, max(len(rows), rate * target_s / max(nprod.mean(), 1))))
+    rows = np.arange(want, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.gustavson_parallel(A, A, threads, rows)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * float(nprod[rows].sum())
+    return flops / dt / 1e9, dt, want
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    A = I.erdos_renyi(1 << 20, 16)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(A, 2.0, threads)
+    vals, secs, rows = [], [], 0
+    for _ in range(args.steps):
+        v, dt, rows = oracle_sample(A, 8.0, threads)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    sample = f"first {rows} of {A.rows} rows of A*A per step (Gustavson, FP64)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_2206_06611_gb300 import brm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    brm.load()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # every rank multiplies its own independent matrix (weak scaling)
+    A = I.erdos_renyi(1 << 20, 16, seed=I.DEFAULT_SEED + rank)
+    vbytes = 8
+    dA = brm.to_device(A, device=f"cuda:{dev}")
+    st = torch.cuda.current_stream()
+
+    # warm-up (also gives the result size)
+    C = None
+    for _ in range(args.warmup):
+        C = brm.brm_spgemm_precise(dA, dA)
+    torch.cuda.synchronize()
+    nnz_c = C.nnz
+    del C
+    nprod_total = brm.brm_row_nprod(dA, dA)[1]
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = Clocks(dev) if rank == 0 else None
+    brm.brm_trace_reset()
+    brm.brm_trace_enable(True)
+    launches0 = brm.brm_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        C = brm.brm_spgemm_precise(dA, dA)
+        del C
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = (brm.brm_kernel_launches() - launches0) / args.steps
+    trace = brm.brm_trace_read()
+    brm.brm_trace_enable(False)
+    clk = clocks.stop() if clocks else None
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * 2.0 * nprod_total * args.steps / (ms_max * 1e-3) / 1e9
+
+    # ---- end to end: host buffers, copies inside the timed region ----------
+    hA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+          for k, v in (("rp", A.rp.astype(np.int32)), ("col", A.col.astype(np.int32)), ("val", A.val))}
+    h2d = sum(t.numel() * t.element_size() for t in hA.values())
+    out_rp = torch.empty(A.rows + 1, dtype=torch.int64).pin_memory()
+    out_col = torch.empty(nnz_c, dtype=torch.int32).pin_memory()
+    out_val = torch.empty(nnz_c, dtype=torch.float64).pin_memory()
+    d2h = out_rp.numel() * 8 + nnz_c * (4 + vbytes)
+    dA2 = brm.DeviceCSR(A.rows, A.cols, torch.empty_like(dA.rp), torch.empty_like(dA.col), torch.empty_like(dA.val))
+    e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    for _ in range(e_steps):
+        dA2.rp.copy_(hA["rp"], non_blocking=True)
+        dA2.col.copy_(hA["col"], non_blocking=True)
+        dA2.val.copy_(hA["val"], non_blocking=True)
+        C = brm.brm_spgemm_precise(dA2, dA2)
+        out_rp.copy_(C.rp, non_blocking=True)
+        out_col.copy_(C.col, non_blocking=True)
+        out_val.copy_(C.val, non_blocking=True)
+        del C
+    f1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    barrier()
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * 2.0 * nprod_total * e_steps / (e2e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    kern = max(("numeric_warp", "numeric_block", "numeric_long", "symbolic_warp"), key=lambda k: trace[k][0])
+    k_ms, k_launch = trace[kern]
+    per_launch_ms = k_ms / max(k_launch, 1)
+    alg_bytes = numeric_bytes(A, A, nnz_c, vbytes) if kern.startswith("numeric") else None
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if alg_bytes else None
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+                "traffic": NUMERIC_WARP_TRAFFIC if kern == "numeric_warp" else None,
+                "algorithmic_bytes": alg_bytes, "kernel_ms": per_launch_ms}
+    phases = {k: round(v[0] / args.steps, 4) for k, v in trace.items() if v[1]}
+
+    # ---- CPU oracle on a bounded sample --------------------------------------
+    cpu = None
+    if not args.no_cpu and world == 1:
+        threads = os.cpu_count() or 1
+        v, dt, rows = oracle_sample(A, args.cpu_seconds, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {rows} of {A.rows} rows of A*A (Gustavson FP64, {dt:.1f} s)"}
+
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": A.rows, "nnz_A": A.nnz, "nprod": nprod_total, "nnz_C": nnz_c,
+                   "global_batch": world, "parallelism": f"independent products x{world}",
+                   "l2": "inputs (205 MB) and output (3.2 GB) exceed L2; no flush"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e_steps},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "phases_ms_per_step": phases,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="brm", choices=["brm", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * brm.h -- C ABI of libbrm, BRMerge row-wise sparse matrix multiplication
+ * C = A * B on CSR matrices for one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the BRMerge accumulation of Du et al., "Accelerating CPU-Based
+ * Sparse General Matrix Multiplication With Binary Row Merging" (IEEE Access
+ * 2022): for every output row the scaled rows A_ik * B_k* are gathered into a
+ * ping-pong buffer (the multiplying phase) and merged two lists at a time in a
+ * binary tree, adjacent pairs (0,1), (2,3), ..., a last odd list copied, equal
+ * columns added (the accumulating phase); Section III-A/B, Algorithm 1,
+ * Fig. 2.  C is sized either from the intermediate-product upper bound and
+ * compacted afterwards (BRMerge-Upper, Section III-D-1) or from a symbolic
+ * pass that counts each row's nonzeros first (BRMerge-Precise, Section
+ * III-D-2, allocation methods of Section II-B).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices: CSR.  Input row pointers and column indices are int32; columns
+ *   must be strictly ascending inside each row (Section II-A: sorted CSR; the
+ *   sortedness of every generated list relies on it, Section III-B).  The
+ *   output row pointer is int64 because nnz(C) may exceed 2^31.
+ * - All array pointers in brm_csr / brm_csr_out are DEVICE pointers on the
+ *   current CUDA device unless a call says otherwise.  Inputs are owned by the
+ *   caller and only read.
+ * - Values: dtype BRM_F64 (double) or BRM_F32 (float); A and B must agree and
+ *   C gets the same dtype.  Products are rounded before they are added and no
+ *   multiply-add is fused, so a row's value is fixed by the merge tree alone.
+ * - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every kernel of a call runs on it.  Calls that must size an output read a
+ *   few scalars back to the host and therefore synchronise the stream (each
+ *   call's comment says how many times).
+ * - Memory: C's arrays and all temporary workspace are obtained through the
+ *   brm_allocator callbacks (for example PyTorch's caching allocator); with a
+ *   NULL allocator the library uses cudaMallocAsync/cudaFreeAsync on the
+ *   stream.  Workspace is released before the call returns.  On error every
+ *   allocation made by the call is released and *C is zeroed.
+ * - Return value: BRM_OK (0) or one of the negative brm_status codes; nothing
+ *   is thrown across the ABI.  brm_last_error() gives a message for the last
+ *   failing call on the calling host thread.
+ */
+#ifndef BRM_H_
+#define BRM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BRM_OK = 0,
+    BRM_ERR_INVALID = -1,   /* malformed CSR (row_ptr, column range/order) or bad argument */
+    BRM_ERR_SHAPE = -2,     /* A.cols != B.rows, or inconsistent sizes */
+    BRM_ERR_DTYPE = -3,     /* unknown dtype, or A and B differ */
+    BRM_ERR_OOM = -4,       /* the allocator returned NULL */
+    BRM_ERR_OVERFLOW = -5,  /* a count exceeds what the index types can hold */
+    BRM_ERR_CUDA = -6,      /* a CUDA runtime call failed (message has the CUDA error) */
+    BRM_ERR_TIMEOUT = -7    /* a bounded device-side wait ran out */
+} brm_status;
+
+typedef enum { BRM_F32 = 0, BRM_F64 = 1 } brm_dtype;
+
+/* Input matrix (rows x cols, nnz entries): row_ptr[rows+1], col_idx[nnz],
+ * val[nnz] of the given dtype.  All device pointers, caller-owned, read only.
+ * val may be NULL only for brm_spgemm_symbolic. */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *val;
+    int32_t dtype;
+} brm_csr;
+
+/* Output matrix filled by the library: row_ptr[rows+1] (int64), col_idx[nnz],
+ * val[nnz].  The arrays come from the brm_allocator of the call and belong to
+ * the caller afterwards (free them with the same allocator). */
+typedef struct {
+    int64_t rows, cols, nnz;
+    int64_t *row_ptr;
+    int32_t *col_idx;
+    void *val;
+    int32_t dtype;
+} brm_csr_out;
+
+/* Device-memory callbacks.  alloc(bytes, ctx) returns a device pointer
+ * aligned to at least 256 bytes, or NULL when out of memory; release(p, ctx)
+ * frees it (p may be NULL).  Memory must be usable by work queued on the
+ * call's stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*release)(void *p, void *ctx);
+    void *ctx;
+} brm_allocator;
+
+/* Tuning and checking options; brm_options_default() fills the defaults.
+ *   validate       1: check both inputs on the device first (row_ptr starts at
+ *                  0, is non-decreasing and ends at nnz; columns in range and
+ *                  strictly ascending per row) and return BRM_ERR_INVALID.
+ *   compensated    BRM_F32 only, 1: every addition of two equal-column
+ *                  elements in the merge tree is TwoSum-compensated (Knuth,
+ *                  TAOCP vol. 2, 4.2.2): each element carries a float
+ *                  running error, the stored value is sum + error.
+ *   warp_max_nprod rows with 0 < nprod <= this (and <= as many lists) are
+ *                  merged by one warp in shared memory (at most 512).
+ *   block_max_nprod rows up to this many products are merged by one thread
+ *                  block in shared memory; longer rows use the device-memory
+ *                  ping-pong arena (bounded by the kernel's shared memory).
+ *   arena_bytes    budget of the device-memory arena for long rows (0 = the
+ *                  library picks 1/8 of free memory, at least enough for the
+ *                  longest row).
+ */
+typedef struct {
+    int32_t validate;
+    int32_t compensated;
+    int32_t warp_max_nprod;
+    int32_t block_max_nprod;
+    size_t arena_bytes;
+} brm_options;
+
+void brm_options_default(brm_options *opts);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *brm_last_error(void);
+
+/* Library version string. */
+const char *brm_version(void);
+
+/*
+ * Symbolic phase of BRMerge-Precise (Section II-B precise allocation, step 3
+ * of Section III-D-2): the number of nonzeros of every row of C = A * B,
+ * computed from the column indices alone, then its prefix sum.
+ *   A, B        inputs (values not read; val may be NULL).
+ *   C_row_ptr   device int64[A.rows + 1], caller-allocated; receives the
+ *               exclusive prefix sum of the row counts (C_row_ptr[0] = 0).
+ *   nnz_C       host int64*, receives nnz(C) = C_row_ptr[A.rows].
+ * Synchronises the stream twice (product counts and bins; nnz(C)), plus once
+ * more when some rows need the device-memory arena (their sizes are read).
+ */
+int brm_spgemm_symbolic(const brm_csr *A, const brm_csr *B, int64_t *C_row_ptr, int64_t *nnz_C,
+                        const brm_options *opts, const brm_allocator *alloc, void *stream);
+
+/*
+ * BRMerge-Precise (Section III-D-2): product counts and binning, the symbolic
+ * pass, the prefix sum into C.row_ptr, exact allocation of C, then the
+ * numeric BRMerge pass (Algorithm 1) writing every row straight into C.
+ * Columns of C are strictly ascending per row; structural zeros (exact
+ * cancellations, stored zeros) are kept.
+ *   C   host struct; receives the allocated device arrays and sizes.
+ * Synchronises the stream three times (bins, nnz(C), a final check that every
+ * numeric row filled exactly its symbolic slot), once more with long rows.
+ */
+int brm_spgemm_precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
+                       const brm_options *opts, const brm_allocator *alloc, void *stream);
+
+/*
+ * BRMerge-Upper (Section III-D-1): product counts, the prefix sum of the
+ * upper bounds nprod_i into a temporary C_bar (nprod columns and values),
+ * the numeric BRMerge pass writing each row and its size into C_bar, the
+ * prefix sum of the row sizes into C.row_ptr, allocation of C and the copy of
+ * C_bar into C.  Same result as brm_spgemm_precise, bit for bit.  C_bar needs
+ * total_nprod * (4 + sizeof(value)) bytes; BRM_ERR_OOM if it cannot be had.
+ * Synchronises the stream three times (bins, nnz(C), final check), once more
+ * with long rows.
+ */
+int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
+                     const brm_options *opts, const brm_allocator *alloc, void *stream);
+
+/* Frees the arrays of a brm_csr_out with the given allocator and zeroes it. */
+void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);
+
+/*
+ * Per-row statistics used by the binning (step 1 of both libraries, Section
+ * III-D; Algorithm 1 line 1): nprod_i = sum over k in A_i* of |B_k*|.
+ *   row_nprod   device int64[A.rows], caller-allocated.
+ *   total_nprod, max_row_nprod, max_row_nnz_A: host int64*, may be NULL.
+ * Synchronises the stream once.
+ */
+int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_t *total_nprod,
+                  int64_t *max_row_nprod, int64_t *max_row_nnz_A, void *stream);
+
+/*
+ * Tracing (the measurement side of the paper's evaluation, Section IV-A: the
+ * time of each part of the computation).  With tracing on, every later call
+ * records CUDA events on its stream around each kernel phase; the elapsed
+ * device times are added per phase when the call returns.  Phases, in order:
+ * validate, bin, symbolic_warp, symbolic_block, symbolic_long, scan,
+ * numeric_warp, numeric_block, numeric_long, compact.  Not thread-safe across
+ * concurrent calls from several host threads.
+ *   brm_trace_enable      on != 0 enables; returns the previous setting.
+ *   brm_trace_reset       zeroes the accumulated times and launch counts.
+ *   brm_trace_read        copies up to n per-phase totals (milliseconds of
+ *                         device time, kernel launches) into host arrays
+ *                         (either may be NULL); returns the number of phases.
+ *   brm_trace_phase_name  name of phase i ("" if out of range).
+ *   brm_kernel_launches   kernel launches made by the library since loading
+ *                         (counted whether tracing is on or not).
+ */
+int brm_trace_enable(int on);
+void brm_trace_reset(void);
+int brm_trace_read(double *ms, int64_t *launches, int n);
+const char *brm_trace_phase_name(int i);
+int64_t brm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRM_H_ */

@@ -1,0 +1,320 @@
+"""Python binding of libbrm (BRMerge SpGEMM for sm_103a) -- argument
+marshalling only.
+
+Every function here forwards to the extern "C" entry point of the same name in
+``libbrm.so`` (declared in ``include/brm.h``).  PyTorch supplies device memory
+(its caching allocator is handed to the library as the brm_allocator callbacks)
+and the stream (the current torch stream); all computation runs in the
+library's CUDA kernels.  There is no fallback: if the library cannot be built
+or loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------------------
+# C structures (mirror include/brm.h)
+# ---------------------------------------------------------------------------
+BRM_OK = 0
+BRM_ERR = {-1: "BRM_ERR_INVALID", -2: "BRM_ERR_SHAPE", -3: "BRM_ERR_DTYPE", -4: "BRM_ERR_OOM",
+           -5: "BRM_ERR_OVERFLOW", -6: "BRM_ERR_CUDA", -7: "BRM_ERR_TIMEOUT"}
+BRM_F32, BRM_F64 = 0, 1
+
+
+class brm_csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32)]
+
+
+class brm_csr_out(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class brm_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class brm_options(ctypes.Structure):
+    _fields_ = [("validate", ctypes.c_int32), ("compensated", ctypes.c_int32),
+                ("warp_max_nprod", ctypes.c_int32), ("block_max_nprod", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_size_t)]
+
+
+class BrmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{BRM_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---------------------------------------------------------------------------
+# library loading
+# ---------------------------------------------------------------------------
+_lib = None
+HEADER = os.path.join(_build.INCLUDE, "brm.h")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libbrm.so (building it first when stale and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libbrm.so is not built ({_build.LIB}); run paper_2206_06611_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    pcsr, pout = ctypes.POINTER(brm_csr), ctypes.POINTER(brm_csr_out)
+    popt, pal = ctypes.POINTER(brm_options), ctypes.POINTER(brm_allocator)
+    lib.brm_options_default.argtypes = [popt]
+    lib.brm_options_default.restype = None
+    lib.brm_last_error.restype = ctypes.c_char_p
+    lib.brm_version.restype = ctypes.c_char_p
+    lib.brm_spgemm_symbolic.argtypes = [pcsr, pcsr, P, ctypes.POINTER(I64), popt, pal, P]
+    lib.brm_spgemm_precise.argtypes = [pcsr, pcsr, pout, popt, pal, P]
+    lib.brm_spgemm_upper.argtypes = [pcsr, pcsr, pout, popt, pal, P]
+    lib.brm_csr_out_free.argtypes = [pout, pal, P]
+    lib.brm_csr_out_free.restype = None
+    lib.brm_row_nprod.argtypes = [pcsr, pcsr, P, P, P, P, P]
+    for f in (lib.brm_spgemm_symbolic, lib.brm_spgemm_precise, lib.brm_spgemm_upper, lib.brm_row_nprod):
+        f.restype = ctypes.c_int
+    lib.brm_trace_enable.argtypes = [ctypes.c_int]
+    lib.brm_trace_enable.restype = ctypes.c_int
+    lib.brm_trace_reset.argtypes = []
+    lib.brm_trace_reset.restype = None
+    lib.brm_trace_read.argtypes = [P, P, ctypes.c_int]
+    lib.brm_trace_read.restype = ctypes.c_int
+    lib.brm_trace_phase_name.argtypes = [ctypes.c_int]
+    lib.brm_trace_phase_name.restype = ctypes.c_char_p
+    lib.brm_kernel_launches.argtypes = []
+    lib.brm_kernel_launches.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/brm.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(brm_[a-z_0-9]+)\s*\(", text, re.M)))
+
+
+def _check(rc: int):
+    if rc != BRM_OK:
+        raise BrmError(rc, load().brm_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# device CSR and marshalling
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class DeviceCSR:
+    """CSR on the GPU: rp (int32 for inputs, int64 for results), col int32, val."""
+    rows: int
+    cols: int
+    rp: "torch.Tensor"
+    col: "torch.Tensor"
+    val: "torch.Tensor | None"
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def to_host(self):
+        from .inputs import CSR
+        val = None if self.val is None else self.val.cpu().numpy()
+        return CSR(self.rows, self.cols, self.rp.cpu().numpy(), self.col.cpu().numpy(), val)
+
+
+def to_device(A, device="cuda", dtype=None) -> DeviceCSR:
+    """Copy a host CSR (paper_2206_06611_gb300.inputs.CSR) to the GPU."""
+    import torch
+    val = A.val if dtype is None else A.val.astype(dtype)
+    return DeviceCSR(A.rows, A.cols,
+                     torch.from_numpy(np.ascontiguousarray(A.rp, dtype=np.int32)).to(device),
+                     torch.from_numpy(np.ascontiguousarray(A.col, dtype=np.int32)).to(device),
+                     torch.from_numpy(np.ascontiguousarray(val)).to(device))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t is None:
+        return BRM_F64
+    if t.dtype == torch.float64:
+        return BRM_F64
+    if t.dtype == torch.float32:
+        return BRM_F32
+    raise TypeError(f"unsupported value dtype {t.dtype}")
+
+
+def _csr_struct(A: DeviceCSR) -> brm_csr:
+    import torch
+    for t, want in ((A.rp, torch.int32), (A.col, torch.int32)):
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("row_ptr and col_idx must be contiguous int32 CUDA tensors")
+    if A.val is not None and (not A.val.is_cuda or not A.val.is_contiguous()):
+        raise TypeError("values must be a contiguous CUDA tensor")
+    return brm_csr(A.rows, A.cols, A.nnz, A.rp.data_ptr(), A.col.data_ptr() if A.nnz else None,
+                   None if A.val is None or A.nnz == 0 else A.val.data_ptr(), _dtype_code(A.val))
+
+
+class TorchAllocator:
+    """brm_allocator backed by torch's caching allocator (current device/stream)."""
+
+    def __init__(self, device=None):
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.live = {}
+        self._alloc_cb = ALLOC_FN(self._alloc)
+        self._release_cb = RELEASE_FN(self._release)
+        self.struct = brm_allocator(self._alloc_cb, self._release_cb, None)
+
+    def _alloc(self, nbytes, ctx):
+        import torch
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except torch.OutOfMemoryError:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _release(self, p, ctx):
+        self.live.pop(p, None)
+
+    def take(self, p, dtype, count):
+        """Hand the allocation at p over to Python as a typed tensor."""
+        t = self.live.pop(p)
+        return t.view(dtype)[:count]
+
+
+_alloc_cache = {}
+
+
+def _allocator():
+    import torch
+    dev = torch.cuda.current_device()
+    if dev not in _alloc_cache:
+        _alloc_cache[dev] = TorchAllocator(dev)
+    return _alloc_cache[dev]
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, arena_bytes=0) -> brm_options:
+    o = brm_options()
+    load().brm_options_default(ctypes.byref(o))
+    o.validate = int(bool(validate))
+    o.compensated = int(bool(compensated))
+    if warp_max_nprod:
+        o.warp_max_nprod = warp_max_nprod
+    if block_max_nprod:
+        o.block_max_nprod = block_max_nprod
+    o.arena_bytes = arena_bytes
+    return o
+
+
+def _result(al: TorchAllocator, C: brm_csr_out, val_dtype) -> DeviceCSR:
+    import torch
+    rp = al.take(C.row_ptr, torch.int64, C.rows + 1)
+    col = al.take(C.col_idx, torch.int32, C.nnz)
+    val = al.take(C.val, val_dtype, C.nnz)
+    return DeviceCSR(C.rows, C.cols, rp, col, val)
+
+
+def brm_spgemm_precise(A: DeviceCSR, B: DeviceCSR, *, compensated=False, validate=False, stream=None,
+                       **opts) -> DeviceCSR:
+    """C = A*B by BRMerge-Precise (symbolic pass, exact allocation, numeric pass)."""
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    o = options(validate=validate, compensated=compensated, **opts)
+    al = _allocator()
+    C = brm_csr_out()
+    _check(lib.brm_spgemm_precise(ctypes.byref(a), ctypes.byref(b), ctypes.byref(C), ctypes.byref(o),
+                                  ctypes.byref(al.struct), _stream(stream)))
+    return _result(al, C, A.val.dtype)
+
+
+def brm_spgemm_upper(A: DeviceCSR, B: DeviceCSR, *, compensated=False, validate=False, stream=None,
+                     **opts) -> DeviceCSR:
+    """C = A*B by BRMerge-Upper (upper-bound C_bar, numeric pass, compaction)."""
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    o = options(validate=validate, compensated=compensated, **opts)
+    al = _allocator()
+    C = brm_csr_out()
+    _check(lib.brm_spgemm_upper(ctypes.byref(a), ctypes.byref(b), ctypes.byref(C), ctypes.byref(o),
+                                ctypes.byref(al.struct), _stream(stream)))
+    return _result(al, C, A.val.dtype)
+
+
+def brm_spgemm_symbolic(A: DeviceCSR, B: DeviceCSR, *, validate=False, stream=None, **opts):
+    """(C.row_ptr as an int64 CUDA tensor, nnz(C))."""
+    import torch
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    o = options(validate=validate, **opts)
+    rp = torch.empty(A.rows + 1, dtype=torch.int64, device=A.rp.device)
+    nnz = ctypes.c_int64(0)
+    _check(lib.brm_spgemm_symbolic(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(rp.data_ptr()),
+                                   ctypes.byref(nnz), ctypes.byref(o), ctypes.byref(_allocator().struct),
+                                   _stream(stream)))
+    return rp, int(nnz.value)
+
+
+def brm_row_nprod(A: DeviceCSR, B: DeviceCSR, *, stream=None):
+    """(per-row product counts int64 tensor, total, max row nprod, max row nnz of A)."""
+    import torch
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    out = torch.empty(max(A.rows, 1), dtype=torch.int64, device=A.rp.device)
+    tot, mx, ml = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.brm_row_nprod(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(out.data_ptr()), ctypes.byref(tot),
+                             ctypes.byref(mx), ctypes.byref(ml), _stream(stream)))
+    return out[:A.rows], int(tot.value), int(mx.value), int(ml.value)
+
+
+# ---------------------------------------------------------------------------
+# tracing
+# ---------------------------------------------------------------------------
+def brm_trace_enable(on: bool = True) -> bool:
+    return bool(load().brm_trace_enable(int(bool(on))))
+
+
+def brm_trace_reset() -> None:
+    load().brm_trace_reset()
+
+
+def brm_trace_read() -> dict:
+    """{phase name: (device milliseconds, kernel launches)} accumulated so far."""
+    lib = load()
+    n = 16
+    ms = (ctypes.c_double * n)()
+    nl = (ctypes.c_int64 * n)()
+    k = lib.brm_trace_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(nl, ctypes.c_void_p), n)
+    return {lib.brm_trace_phase_name(i).decode(): (ms[i], nl[i]) for i in range(k)}
+
+
+def brm_kernel_launches() -> int:
+    return int(load().brm_kernel_launches())

@@ -1,0 +1,635 @@
+// Host side of libbrm: argument checks, the BRMerge-Upper / BRMerge-Precise
+// pipelines (Section III-D), workspace through the caller's allocator, and the
+// extern "C" entry points declared in include/brm.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "brm.h"
+#include "brm_engine.cuh"
+#include "brm_internal.h"
+
+namespace brm {
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+// ---------------------------------------------------------------------------
+// Tracer: when enabled, CUDA events are recorded on the call's stream around
+// every kernel phase; their elapsed times are added up per phase once the
+// call has synchronised.  Meant for one host thread at a time.
+// ---------------------------------------------------------------------------
+struct Trace {
+    bool on = false;
+    double ms[kNumPhases] = {};
+    long long launches[kNumPhases] = {};
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int ph; long long nl; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::mutex mu;
+
+    cudaEvent_t event() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return e;
+    }
+    void flush() {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Rec &r : pending) {
+            float t = 0.0f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+                ms[r.ph] += t;
+                launches[r.ph] += r.nl;
+            } else {
+                cudaGetLastError();
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+};
+Trace g_trace;
+
+struct PhaseScope {
+    int ph;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    long long n0;
+    PhaseScope(int phase, cudaStream_t s) : ph(phase), st(s), n0(g_launches.load()) {
+        if (g_trace.on) {
+            std::lock_guard<std::mutex> lk(g_trace.mu);
+            a = g_trace.event();
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~PhaseScope() {
+        if (!a) return;
+        std::lock_guard<std::mutex> lk(g_trace.mu);
+        cudaEvent_t b = g_trace.event();
+        if (!b) { g_trace.pool.push_back(a); return; }
+        cudaEventRecord(b, st);
+        g_trace.pending.push_back({ph, g_launches.load() - n0, a, b});
+    }
+};
+
+#define BRM_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(BRM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device memory of one call.  Everything still owned at destruction (error
+// paths, workspace) is released; arrays handed to the caller are detached.
+struct Mem {
+    const brm_allocator *al;
+    cudaStream_t st;
+    std::vector<void *> owned;
+
+    Mem(const brm_allocator *a, cudaStream_t s) : al(a), st(s) {}
+    ~Mem() { release_all(); }
+
+    void *get(size_t bytes) {
+        if (bytes == 0) bytes = 256;
+        void *p = nullptr;
+        if (al && al->alloc) {
+            p = al->alloc(bytes, al->ctx);
+        } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) owned.push_back(p);
+        return p;
+    }
+    void free_one(void *p) {
+        if (!p) return;
+        auto it = std::find(owned.begin(), owned.end(), p);
+        if (it != owned.end()) owned.erase(it);
+        release(p);
+    }
+    void release(void *p) {
+        if (al && al->release) al->release(p, al->ctx);
+        else if (!al || !al->alloc) cudaFreeAsync(p, st);
+    }
+    void detach(void *p) {
+        auto it = std::find(owned.begin(), owned.end(), p);
+        if (it != owned.end()) owned.erase(it);
+    }
+    void release_all() {
+        for (void *p : owned) release(p);
+        owned.clear();
+    }
+};
+
+template <class T>
+int get(Mem &mem, T *&p, size_t count, const char *what) {
+    p = static_cast<T *>(mem.get(count * sizeof(T)));
+    if (!p) return fail(BRM_ERR_OOM, "allocation of %zu bytes for %s failed", count * sizeof(T), what);
+    return BRM_OK;
+}
+
+int check_csr(const brm_csr *M, const char *name, bool need_val) {
+    if (!M) return fail(BRM_ERR_INVALID, "%s is NULL", name);
+    if (M->rows < 0 || M->cols < 0 || M->nnz < 0) return fail(BRM_ERR_INVALID, "%s has a negative size", name);
+    if (M->rows >= INT32_MAX || M->cols >= INT32_MAX || M->nnz > INT32_MAX)
+        return fail(BRM_ERR_OVERFLOW, "%s exceeds the int32 index range", name);
+    if (!M->row_ptr) return fail(BRM_ERR_INVALID, "%s.row_ptr is NULL", name);
+    if (M->nnz > 0 && !M->col_idx) return fail(BRM_ERR_INVALID, "%s.col_idx is NULL", name);
+    if (need_val && M->nnz > 0 && !M->val) return fail(BRM_ERR_INVALID, "%s.val is NULL", name);
+    if (M->dtype != BRM_F32 && M->dtype != BRM_F64) return fail(BRM_ERR_DTYPE, "%s has unknown dtype %d", name, M->dtype);
+    return BRM_OK;
+}
+
+int check_pair(const brm_csr *A, const brm_csr *B, bool need_val) {
+    int rc = check_csr(A, "A", need_val);
+    if (rc) return rc;
+    if ((rc = check_csr(B, "B", need_val))) return rc;
+    if (A->cols != B->rows)
+        return fail(BRM_ERR_SHAPE, "A is %lld x %lld but B is %lld x %lld", (long long)A->rows, (long long)A->cols,
+                    (long long)B->rows, (long long)B->cols);
+    if (need_val && A->dtype != B->dtype) return fail(BRM_ERR_DTYPE, "A and B have different dtypes");
+    return BRM_OK;
+}
+
+brm_options resolve(const brm_options *o) {
+    brm_options r;
+    brm_options_default(&r);
+    if (o) r = *o;
+    if (r.warp_max_nprod <= 0 || r.warp_max_nprod > kWarpCap) r.warp_max_nprod = kWarpCap;
+    if (r.block_max_nprod <= 0 || r.block_max_nprod > kBlockCap) r.block_max_nprod = kBlockCap;
+    if (r.block_max_nprod < r.warp_max_nprod) r.block_max_nprod = r.warp_max_nprod;
+    return r;
+}
+
+// Result of the binning step.
+struct Plan {
+    BinStats stats{};
+    int32_t *bin_rows[kNumBins] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t *long_nprod = nullptr;      // device, per long slot (binning order)
+    int32_t *long_L = nullptr;
+    int32_t *long_rows_s = nullptr;     // device, long rows sorted by nprod (descending)
+    int64_t *long_nprod_s = nullptr;
+    std::vector<int32_t> long_rows_h;   // host copies, same order
+    std::vector<int64_t> long_nprod_h;
+    std::vector<int32_t> long_L_h;
+};
+
+int validate_inputs(Mem &mem, const brm_csr *A, const brm_csr *B) {
+    BinStats *st;
+    int rc = get(mem, st, 1, "validation flag");
+    if (rc) return rc;
+    BRM_CUDA(cudaMemsetAsync(st, 0, sizeof(BinStats), mem.st));
+    {
+        PhaseScope ps(kPhValidate, mem.st);
+        BRM_CUDA(launch_validate(A->rows, A->cols, A->nnz, A->row_ptr, A->col_idx, st, mem.st));
+        BRM_CUDA(launch_validate(B->rows, B->cols, B->nnz, B->row_ptr, B->col_idx, st, mem.st));
+    }
+    BinStats h{};
+    BRM_CUDA(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    mem.free_one(st);
+    if (h.bad) return fail(BRM_ERR_INVALID, "malformed CSR input (row_ptr or column order/range)");
+    return BRM_OK;
+}
+
+// Step 1 (+ the GPU form of step 2): product counts, bins, long-row order.
+int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o, Plan &pl, int64_t *nprod,
+              int64_t *row_cnt) {
+    const int64_t m = A->rows;
+    BinStats *st;
+    int rc = get(mem, st, 1, "bin statistics");
+    if (rc) return rc;
+    BRM_CUDA(cudaMemsetAsync(st, 0, sizeof(BinStats), mem.st));
+    for (int b = kBinWarp; b < kNumBins; ++b)
+        if ((rc = get(mem, pl.bin_rows[b], (size_t)std::max<int64_t>(m, 1), "bin row list"))) return rc;
+    if ((rc = get(mem, pl.long_nprod, (size_t)std::max<int64_t>(m, 1), "long-row sizes"))) return rc;
+    if ((rc = get(mem, pl.long_L, (size_t)std::max<int64_t>(m, 1), "long-row list counts"))) return rc;
+    BinArgs a{};
+    a.m = m;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.brp = B->row_ptr;
+    a.warp_cap = o.warp_max_nprod;
+    a.block_cap = o.block_max_nprod;
+    a.block_lcap = kBlockLCap;
+    a.nprod = nprod;
+    for (int b = 0; b < kNumBins; ++b) a.bin_rows[b] = pl.bin_rows[b];
+    a.long_nprod = pl.long_nprod;
+    a.long_L = pl.long_L;
+    a.row_cnt = row_cnt;
+    a.st = st;
+    {
+        PhaseScope ps(kPhBin, mem.st);
+        BRM_CUDA(launch_bin(a, mem.st));
+    }
+    BRM_CUDA(cudaMemcpyAsync(&pl.stats, st, sizeof(BinStats), cudaMemcpyDeviceToHost, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    mem.free_one(st);
+    if (pl.stats.max_nprod >= (unsigned long long)INT32_MAX)
+        return fail(BRM_ERR_OVERFLOW, "a row has %llu intermediate products (limit 2^31-1)", pl.stats.max_nprod);
+    const int64_t nl = (int64_t)pl.stats.count[kBinLong];
+    if (nl > 0) {
+        std::vector<int32_t> rows(nl), Ls(nl);
+        std::vector<int64_t> np(nl);
+        BRM_CUDA(cudaMemcpyAsync(rows.data(), pl.bin_rows[kBinLong], nl * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 mem.st));
+        BRM_CUDA(cudaMemcpyAsync(np.data(), pl.long_nprod, nl * sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
+        BRM_CUDA(cudaMemcpyAsync(Ls.data(), pl.long_L, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, mem.st));
+        BRM_CUDA(cudaStreamSynchronize(mem.st));
+        // largest rows first, so that the longest merges start earliest
+        std::vector<int64_t> idx(nl);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return np[x] > np[y]; });
+        pl.long_rows_h.resize(nl);
+        pl.long_nprod_h.resize(nl);
+        pl.long_L_h.resize(nl);
+        for (int64_t s = 0; s < nl; ++s) {
+            pl.long_rows_h[s] = rows[idx[s]];
+            pl.long_nprod_h[s] = np[idx[s]];
+            pl.long_L_h[s] = Ls[idx[s]];
+        }
+        if ((rc = get(mem, pl.long_rows_s, nl, "long rows"))) return rc;
+        if ((rc = get(mem, pl.long_nprod_s, nl, "long-row sizes"))) return rc;
+        BRM_CUDA(cudaMemcpyAsync(pl.long_rows_s, pl.long_rows_h.data(), nl * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 mem.st));
+        BRM_CUDA(cudaMemcpyAsync(pl.long_nprod_s, pl.long_nprod_h.data(), nl * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, mem.st));
+        BRM_CUDA(cudaStreamSynchronize(mem.st));   // host vectors must outlive the copies
+    }
+    return BRM_OK;
+}
+
+// One BRMerge pass (symbolic or numeric) over all bins.
+int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
+    for (int b = kBinWarp; b <= kBinBlock; ++b) {
+        RowJob jb = j;
+        jb.rows = pl.bin_rows[b];
+        jb.count = (int32_t)pl.stats.count[b];
+        if (jb.count == 0) continue;
+        PhaseScope ps((v == kIdx ? kPhSymWarp : kPhNumWarp) + (b - kBinWarp), mem.st);
+        BRM_CUDA(launch_rows(v, b, jb, mem.st));
+    }
+    const int64_t nl = (int64_t)pl.long_rows_h.size();
+    if (nl == 0) return BRM_OK;
+    // batches of long rows whose arena slices fit the budget
+    std::vector<int64_t> need(nl);
+    size_t biggest = 0;
+    for (int64_t s = 0; s < nl; ++s) {
+        need[s] = (int64_t)long_row_bytes_for(v, pl.long_nprod_h[s], pl.long_L_h[s]);
+        biggest = std::max(biggest, (size_t)need[s]);
+    }
+    size_t budget = o.arena_bytes;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = (size_t)8 << 30; }
+        budget = std::min<size_t>(fr / 8, (size_t)32 << 30);
+    }
+    budget = std::max(budget, biggest);
+    std::vector<int64_t> off(nl);
+    std::vector<int64_t> starts;
+    size_t cur = 0, maxbatch = 0;
+    for (int64_t s = 0; s < nl; ++s) {
+        if (s == 0 || cur + (size_t)need[s] > budget) {
+            starts.push_back(s);
+            cur = 0;
+        }
+        off[s] = (int64_t)cur;
+        cur += (size_t)need[s];
+        maxbatch = std::max(maxbatch, cur);
+    }
+    starts.push_back(nl);
+    int64_t *off_d;
+    int rc = get(mem, off_d, nl, "arena offsets");
+    if (rc) return rc;
+    char *arena;
+    if ((rc = get(mem, arena, maxbatch, "long-row arena"))) return rc;
+    BRM_CUDA(cudaMemcpyAsync(off_d, off.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
+    PhaseScope ps(v == kIdx ? kPhSymLong : kPhNumLong, mem.st);
+    for (size_t bi = 0; bi + 1 < starts.size(); ++bi) {
+        RowJob jb = j;
+        jb.rows = pl.long_rows_s + starts[bi];
+        jb.count = (int32_t)(starts[bi + 1] - starts[bi]);
+        jb.arena = arena;
+        jb.arena_off = off_d + starts[bi];
+        jb.slot_nprod = pl.long_nprod_s + starts[bi];
+        BRM_CUDA(launch_rows(v, kBinLong, jb, mem.st));
+    }
+    BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
+    mem.free_one(arena);
+    mem.free_one(off_d);
+    return BRM_OK;
+}
+
+// Reads the row-length flag of a numeric pass (synchronises the stream).
+int check_flag(Mem &mem, const unsigned int *err) {
+    unsigned int h = 0;
+    BRM_CUDA(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    if (h) return fail(BRM_ERR_INVALID, "a numeric row length disagrees with its symbolic count");
+    return BRM_OK;
+}
+
+RowJob base_job(const brm_csr *A, const brm_csr *B) {
+    RowJob j{};
+    j.arp = A->row_ptr;
+    j.acol = A->col_idx;
+    j.aval = A->val;
+    j.brp = B->row_ptr;
+    j.bcol = B->col_idx;
+    j.bval = B->val;
+    return j;
+}
+
+VKind value_kind(const brm_csr *A, const brm_options &o) {
+    if (A->dtype == BRM_F64) return kF64;
+    return o.compensated ? kF32C : kF32;
+}
+
+size_t value_bytes(int32_t dtype) { return dtype == BRM_F64 ? 8 : 4; }
+
+// Symbolic phase into row_ptr (m+1, device); returns nnz(C) on the host.
+int symbolic_into(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o, Plan &pl, int64_t *row_ptr,
+                  int64_t *nnz) {
+    const int64_t m = A->rows;
+    int64_t *row_nnz;
+    int rc = get(mem, row_nnz, (size_t)std::max<int64_t>(m, 1), "row counts");
+    if (rc) return rc;
+    if ((rc = make_plan(mem, A, B, o, pl, nullptr, row_nnz))) return rc;
+    RowJob j = base_job(A, B);
+    j.out_cnt = row_nnz;
+    if ((rc = run_pass(mem, kIdx, pl, o, j))) return rc;
+    void *tmp;
+    if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
+    {
+        PhaseScope ps(kPhScan, mem.st);
+        BRM_CUDA(launch_scan(row_nnz, row_ptr, m, tmp, mem.st));
+    }
+    BRM_CUDA(cudaMemcpyAsync(nnz, row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    mem.free_one(tmp);
+    mem.free_one(row_nnz);
+    return BRM_OK;
+}
+
+int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options *opts, const brm_allocator *al,
+            cudaStream_t st) {
+    if (!C) return fail(BRM_ERR_INVALID, "C is NULL");
+    std::memset(C, 0, sizeof *C);
+    int rc = check_pair(A, B, true);
+    if (rc) return rc;
+    const brm_options o = resolve(opts);
+    Mem mem(al, st);
+    if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
+    const int64_t m = A->rows;
+    int64_t *rp;
+    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    Plan pl;
+    int64_t nnz = 0;
+    if ((rc = symbolic_into(mem, A, B, o, pl, rp, &nnz))) return rc;
+    int32_t *col;
+    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
+    if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
+    RowJob j = base_job(A, B);
+    j.out_rp = rp;
+    j.out_col = col;
+    j.out_val = val;
+    unsigned int *err;
+    if ((rc = get(mem, err, 1, "error flag"))) return rc;
+    BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
+    j.err = err;
+    if ((rc = run_pass(mem, value_kind(A, o), pl, o, j))) return rc;
+    if ((rc = check_flag(mem, err))) return rc;
+    mem.detach(rp);
+    mem.detach(col);
+    mem.detach(val);
+    C->rows = m;
+    C->cols = B->cols;
+    C->nnz = nnz;
+    C->row_ptr = rp;
+    C->col_idx = col;
+    C->val = val;
+    C->dtype = A->dtype;
+    return BRM_OK;
+}
+
+int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options *opts, const brm_allocator *al,
+          cudaStream_t st) {
+    if (!C) return fail(BRM_ERR_INVALID, "C is NULL");
+    std::memset(C, 0, sizeof *C);
+    int rc = check_pair(A, B, true);
+    if (rc) return rc;
+    const brm_options o = resolve(opts);
+    Mem mem(al, st);
+    if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
+    const int64_t m = A->rows;
+    const size_t vb = value_bytes(A->dtype);
+    int64_t *nprod, *row_size, *cbar_off, *rp;
+    if ((rc = get(mem, nprod, (size_t)std::max<int64_t>(m, 1), "row nprod"))) return rc;
+    if ((rc = get(mem, row_size, (size_t)std::max<int64_t>(m, 1), "row sizes"))) return rc;
+    if ((rc = get(mem, cbar_off, (size_t)m + 1, "C_bar offsets"))) return rc;
+    Plan pl;
+    if ((rc = make_plan(mem, A, B, o, pl, nprod, row_size))) return rc;
+    void *tmp;
+    if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
+    // steps 1 and 3: prefix sum of the upper bounds, temporary C_bar
+    {
+        PhaseScope ps(kPhScan, mem.st);
+        BRM_CUDA(launch_scan(nprod, cbar_off, m, tmp, mem.st));
+    }
+    const int64_t total = (int64_t)pl.stats.total_nprod;
+    int32_t *ccol;
+    if ((rc = get(mem, ccol, (size_t)std::max<int64_t>(total, 1), "C_bar columns"))) return rc;
+    void *cval = mem.get((size_t)std::max<int64_t>(total, 1) * vb);
+    if (!cval) return fail(BRM_ERR_OOM, "allocation of C_bar values (%lld products) failed", (long long)total);
+    // step 4: BRMerge into C_bar, recording the row sizes
+    RowJob j = base_job(A, B);
+    j.out_rp = cbar_off;
+    j.out_col = ccol;
+    j.out_val = cval;
+    j.out_cnt = row_size;
+    unsigned int *err;
+    if ((rc = get(mem, err, 1, "error flag"))) return rc;
+    BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
+    j.err = err;
+    if ((rc = run_pass(mem, value_kind(A, o), pl, o, j))) return rc;
+    // step 5: prefix sum of the row sizes, allocation of C
+    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    {
+        PhaseScope ps(kPhScan, mem.st);
+        BRM_CUDA(launch_scan(row_size, rp, m, tmp, mem.st));
+    }
+    int64_t nnz = 0;
+    BRM_CUDA(cudaMemcpyAsync(&nnz, rp + m, sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    int32_t *col;
+    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * vb);
+    if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
+    // step 6: copy C_bar into C
+    {
+        PhaseScope ps(kPhCompact, mem.st);
+        BRM_CUDA(launch_compact(m, cbar_off, rp, ccol, cval, col, val, vb, mem.st));
+    }
+    if ((rc = check_flag(mem, err))) return rc;
+    mem.detach(rp);
+    mem.detach(col);
+    mem.detach(val);
+    C->rows = m;
+    C->cols = B->cols;
+    C->nnz = nnz;
+    C->row_ptr = rp;
+    C->col_idx = col;
+    C->val = val;
+    C->dtype = A->dtype;
+    return BRM_OK;
+}
+
+}  // namespace
+}  // namespace brm
+
+using namespace brm;
+
+extern "C" {
+
+void brm_options_default(brm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->validate = 0;
+    o->compensated = 0;
+    o->warp_max_nprod = kWarpCap;
+    o->block_max_nprod = kBlockCap;
+    o->arena_bytes = 0;
+}
+
+const char *brm_last_error(void) { return g_err.c_str(); }
+
+const char *brm_version(void) { return "brm 0.1 (sm_103a)"; }
+
+int brm_spgemm_precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options *opts,
+                       const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    const int rc = precise(A, B, C, opts, alloc, static_cast<cudaStream_t>(stream));
+    g_trace.flush();
+    return rc;
+}
+
+int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options *opts,
+                     const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    const int rc = upper(A, B, C, opts, alloc, static_cast<cudaStream_t>(stream));
+    g_trace.flush();
+    return rc;
+}
+
+int brm_spgemm_symbolic(const brm_csr *A, const brm_csr *B, int64_t *C_row_ptr, int64_t *nnz_C,
+                        const brm_options *opts, const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    int rc = check_pair(A, B, false);
+    if (rc) return rc;
+    if (!C_row_ptr || !nnz_C) return fail(BRM_ERR_INVALID, "C_row_ptr and nnz_C must not be NULL");
+    const brm_options o = resolve(opts);
+    Mem mem(alloc, static_cast<cudaStream_t>(stream));
+    if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
+    Plan pl;
+    rc = symbolic_into(mem, A, B, o, pl, C_row_ptr, nnz_C);
+    g_trace.flush();
+    return rc;
+}
+
+void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream) {
+    if (!C) return;
+    Mem mem(alloc, static_cast<cudaStream_t>(stream));
+    if (C->row_ptr) mem.release(C->row_ptr);
+    if (C->col_idx) mem.release(C->col_idx);
+    if (C->val) mem.release(C->val);
+    std::memset(C, 0, sizeof *C);
+}
+
+int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_t *total_nprod,
+                  int64_t *max_row_nprod, int64_t *max_row_nnz_A, void *stream) {
+    g_err.clear();
+    int rc = check_pair(A, B, false);
+    if (rc) return rc;
+    if (!row_nprod && A->rows > 0) return fail(BRM_ERR_INVALID, "row_nprod is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Mem mem(nullptr, st);
+    BinStats *bs;
+    if ((rc = get(mem, bs, 1, "statistics"))) return rc;
+    BRM_CUDA(cudaMemsetAsync(bs, 0, sizeof(BinStats), st));
+    BinArgs a{};
+    a.m = A->rows;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.brp = B->row_ptr;
+    a.warp_cap = kWarpCap;
+    a.block_cap = kBlockCap;
+    a.block_lcap = kBlockLCap;
+    a.nprod = row_nprod;
+    a.st = bs;
+    {
+        PhaseScope ps(kPhBin, st);
+        BRM_CUDA(launch_bin(a, st));
+    }
+    BinStats h{};
+    BRM_CUDA(cudaMemcpyAsync(&h, bs, sizeof h, cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    if (total_nprod) *total_nprod = (int64_t)h.total_nprod;
+    if (max_row_nprod) *max_row_nprod = (int64_t)h.max_nprod;
+    if (max_row_nnz_A) *max_row_nnz_A = (int64_t)h.max_L;
+    g_trace.flush();
+    return BRM_OK;
+}
+
+static const char *kPhaseNames[kNumPhases] = {
+    "validate", "bin", "symbolic_warp", "symbolic_block", "symbolic_long", "scan",
+    "numeric_warp", "numeric_block", "numeric_long", "compact"};
+
+int brm_trace_enable(int on) {
+    const int was = g_trace.on ? 1 : 0;
+    g_trace.on = on != 0;
+    return was;
+}
+
+void brm_trace_reset(void) {
+    g_trace.flush();
+    std::lock_guard<std::mutex> lk(g_trace.mu);
+    for (int i = 0; i < kNumPhases; ++i) {
+        g_trace.ms[i] = 0.0;
+        g_trace.launches[i] = 0;
+    }
+}
+
+int brm_trace_read(double *ms, int64_t *launches, int n) {
+    g_trace.flush();
+    std::lock_guard<std::mutex> lk(g_trace.mu);
+    for (int i = 0; i < n && i < kNumPhases; ++i) {
+        if (ms) ms[i] = g_trace.ms[i];
+        if (launches) launches[i] = g_trace.launches[i];
+    }
+    return kNumPhases;
+}
+
+const char *brm_trace_phase_name(int i) { return (i >= 0 && i < kNumPhases) ? kPhaseNames[i] : ""; }
+
+int64_t brm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

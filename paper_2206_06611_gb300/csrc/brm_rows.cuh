@@ -1,0 +1,165 @@
+// Row kernels of the three row bins, built on the BRMerge row engine.
+//
+//   warp bin   0 < nprod_i <= WCAP, L_i <= WCAP: one warp per row, ping-pong
+//              buffers and list offsets in the warp's slice of shared memory.
+//   block bin  nprod_i <= BCAP, L_i <= BLCAP: one thread block per row,
+//              buffers in shared memory.
+//   long bin   everything else: one thread block per row, buffers in a
+//              device-memory arena slice given per row by the host.
+// Rows are taken from the bin's row list in a grid-stride loop.
+#pragma once
+
+#include "brm_engine.cuh"
+#include "brm_internal.h"
+
+namespace brm {
+
+constexpr int kWarpK = 8;        // diagonals per thread per tile, warp kernel
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlockThreads = 256;
+constexpr int kBlockK = 8;
+constexpr int kLongThreads = 512;
+constexpr int kLongK = 8;
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Shared-memory bytes of one row buffer pair holding `cap` elements and
+// `lcap` lists: two value arrays, two column arrays, two offset arrays.
+template <class P>
+__host__ __device__ constexpr size_t pair_bytes(int cap, int lcap) {
+    return (P::kVal ? align_up(2 * sizeof(typename P::T) * (size_t)cap, 16) : 0) +
+           align_up(2 * sizeof(int32_t) * (size_t)cap, 16) + align_up(2 * sizeof(int32_t) * (size_t)(lcap + 1), 16);
+}
+
+template <class P>
+__device__ __forceinline__ void carve(unsigned char *p, int cap, int lcap, Buf<P> &b0, Buf<P> &b1) {
+    using T = typename P::T;
+    if constexpr (P::kVal) {
+        b0.val = reinterpret_cast<T *>(p);
+        b1.val = b0.val + cap;
+        p += align_up(2 * sizeof(T) * (size_t)cap, 16);
+    } else {
+        b0.val = nullptr;
+        b1.val = nullptr;
+    }
+    b0.col = reinterpret_cast<int32_t *>(p);
+    b1.col = b0.col + cap;
+    p += align_up(2 * sizeof(int32_t) * (size_t)cap, 16);
+    b0.off = reinterpret_cast<int32_t *>(p);
+    b1.off = b0.off + (lcap + 1);
+}
+
+template <class P, int WCAP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rows_warp(RowJob j) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wid = threadIdx.x >> 5;
+    Buf<P> b0, b1;
+    carve<P>(smem + (size_t)wid * pair_bytes<P>(WCAP, WCAP), WCAP, WCAP, b0, b1);
+    const WarpGrp g;
+    for (int r = blockIdx.x * kWarpsPerBlock + wid; r < j.count; r += gridDim.x * kWarpsPerBlock) {
+        const int row = j.rows[r];
+        int len;
+        const int which = brm_row<P, WarpGrp, kWarpK>(g, row, j, b0, b1, len);
+        store_row<P, WarpGrp>(g, row, j, which ? b1 : b0, len);
+    }
+}
+
+template <class P, int BCAP, int BLCAP>
+__global__ void __launch_bounds__(kBlockThreads) k_rows_block(RowJob j) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int ws[kBlockThreads / 32 + 1];
+    Buf<P> b0, b1;
+    carve<P>(smem, BCAP, BLCAP, b0, b1);
+    BlockGrp<kBlockThreads> g;
+    g.ws = ws;
+    for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
+        const int row = j.rows[r];
+        int len;
+        const int which = brm_row<P, BlockGrp<kBlockThreads>, kBlockK>(g, row, j, b0, b1, len);
+        store_row<P, BlockGrp<kBlockThreads>>(g, row, j, which ? b1 : b0, len);
+    }
+}
+
+// Arena layout of one long row with n products and L lists (host and device
+// agree on it through this function).
+template <class P>
+__host__ __device__ constexpr size_t long_row_bytes(int64_t n, int64_t L) {
+    return (P::kVal ? align_up(2 * sizeof(typename P::T) * (size_t)n, 256) : 0) +
+           align_up(2 * sizeof(int32_t) * (size_t)n, 256) + align_up(2 * sizeof(int32_t) * (size_t)(L + 1), 256);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
+    __shared__ int ws[kLongThreads / 32 + 1];
+    BlockGrp<kLongThreads> g;
+    g.ws = ws;
+    using T = typename P::T;
+    for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
+        const int row = j.rows[r];
+        const int64_t n = j.slot_nprod[r];
+        const int L = j.arp[row + 1] - j.arp[row];
+        unsigned char *p = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[r];
+        Buf<P> b0, b1;
+        if constexpr (P::kVal) {
+            b0.val = reinterpret_cast<T *>(p);
+            b1.val = b0.val + n;
+            p += align_up(2 * sizeof(T) * (size_t)n, 256);
+        } else {
+            b0.val = nullptr;
+            b1.val = nullptr;
+        }
+        b0.col = reinterpret_cast<int32_t *>(p);
+        b1.col = b0.col + n;
+        p += align_up(2 * sizeof(int32_t) * (size_t)n, 256);
+        b0.off = reinterpret_cast<int32_t *>(p);
+        b1.off = b0.off + (L + 1);
+        int len;
+        const int which = brm_row<P, BlockGrp<kLongThreads>, kLongK>(g, row, j, b0, b1, len);
+        store_row<P, BlockGrp<kLongThreads>>(g, row, j, which ? b1 : b0, len);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (grid sized to the SM count times the resident blocks per SM).
+// ---------------------------------------------------------------------------
+template <class P>
+cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
+    if (j.count <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (bin == kBinWarp) {
+        const size_t sm = kWarpsPerBlock * pair_bytes<P>(kWarpCap, kWarpCap);
+        auto kern = k_rows_warp<P, kWarpCap>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, sm);
+        const int need = (j.count + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const int grid = max(1, min(need, sms * max(occ, 1)));
+        kern<<<grid, kWarpsPerBlock * 32, sm, st>>>(j);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        return cudaGetLastError();
+    }
+    if (bin == kBinBlock) {
+        const size_t sm = pair_bytes<P>(kBlockCap, kBlockLCap);
+        auto kern = k_rows_block<P, kBlockCap, kBlockLCap>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlockThreads, sm);
+        const int grid = max(1, min(j.count, sms * max(occ, 1)));
+        kern<<<grid, kBlockThreads, sm, st>>>(j);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        return cudaGetLastError();
+    }
+    // long rows: one block per row of the batch
+    k_rows_long<P><<<j.count, kLongThreads, 0, st>>>(j);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <class P>
+size_t long_bytes_t(int64_t n, int64_t L) { return long_row_bytes<P>(n, L); }
+
+}  // namespace brm
