@@ -318,6 +318,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """One warm-up call and one timed call of the workload, nothing else (the
+    command ncu captures)."""
+    import torch
+    from paper_2206_06611_gb300 import brm
+    torch.cuda.set_device(0)
+    A = I.erdos_renyi(args.profile_n, 16)
+    dA = brm.to_device(A, device="cuda:0")
+    for _ in range(2):
+        C = brm.brm_spgemm_precise(dA, dA)
+        torch.cuda.synchronize()
+        del C
+    print(json.dumps({"profile": "ER", "n": A.rows, "launches": brm.brm_kernel_launches()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,8 +341,12 @@ def main():
     ap.add_argument("--impl", default="brm", choices=["brm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", action="store_true", help="two calls only (for ncu captures)")
+    ap.add_argument("--profile-n", type=int, default=1 << 20)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

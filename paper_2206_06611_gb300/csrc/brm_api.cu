@@ -416,6 +416,7 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
+    j.exact = 1;
     if ((rc = run_pass(mem, value_kind(A, o), pl, o, j))) return rc;
     if ((rc = check_flag(mem, err))) return rc;
     mem.detach(rp);

@@ -156,6 +156,7 @@ struct RowJob {
     void *out_val;
     int64_t *out_cnt;           // optional: receives each row's length
     unsigned int *err;          // set to 1 if a row's length disagrees with its slot
+    int32_t exact;              // 1: a numeric row must fill its slot exactly (Precise)
     // long rows only: per slot, the arena offset (bytes) and the product count
     char *arena;
     const int64_t *arena_off;
@@ -174,18 +175,34 @@ __device__ __forceinline__ int find_last_le(const int32_t *off, int L, int p) {
 
 // ---------------------------------------------------------------------------
 // Multiplying phase.  Fills b.off[0..L] and the N products; returns N.
+// First every list's descriptor is read once (k = A's column, the start of
+// B_k* and its length, A_ik) with one thread per list, and the list ends are
+// prefix-summed; the descriptors are parked in the other buffer (`spare`,
+// unused until the first merge).  Then every thread gathers UNR products at
+// a time -- positions p, p + G, p + 2G, ... so that a group reads a B row
+// with consecutive threads -- issuing all loads before using any.
 // ---------------------------------------------------------------------------
-template <class P, class G>
+template <class P, class G, int UNR>
 __device__ __forceinline__ int multiply_phase(const G &g, int L, const int32_t *__restrict__ acol,
                                               const typename P::In *__restrict__ aval,
                                               const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
-                                              const typename P::In *__restrict__ bval, Buf<P> b) {
+                                              const typename P::In *__restrict__ bval, const Buf<P> b,
+                                              const Buf<P> spare) {
+    using In = typename P::In;
+    int32_t *q0s = spare.off;                                   // L entries
+    In *as = reinterpret_cast<In *>(spare.val);                 // L entries (capacity >= L)
     int carry = 0;
     if (g.rank() == 0) b.off[0] = 0;
     for (int base = 0; base < L; base += G::N) {
         const int t = base + g.rank();
         int len = 0;
-        if (t < L) { const int k = acol[t]; len = brp[k + 1] - brp[k]; }
+        if (t < L) {
+            const int k = acol[t];
+            const int q0 = brp[k];
+            len = brp[k + 1] - q0;
+            q0s[t] = q0;
+            if constexpr (P::kVal) as[t] = aval[t];
+        }
         int tot;
         const int ex = g.scan_excl(len, tot);
         if (t < L) b.off[t + 1] = carry + ex + len;
@@ -193,36 +210,83 @@ __device__ __forceinline__ int multiply_phase(const G &g, int L, const int32_t *
     }
     g.sync();
     const int N = carry;
-    int t = -1, lo = 0, hi = 0, q0 = 0;
-    typename P::In a = typename P::In();
-    for (int p = g.rank(); p < N; p += G::N) {
-        if (p >= hi) {
-            if (t >= 0) {
-                int s = 0;
-                while (s < 4 && b.off[t + 1] <= p) { ++t; ++s; }
-                if (b.off[t + 1] <= p) t = t + find_last_le(b.off + t, L - t, p);
-            } else {
-                t = find_last_le(b.off, L, p);
+    for (int base = 0; base < N; base += G::N * UNR) {
+        int q[UNR];
+        In a[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int p = base + u * G::N + g.rank();
+            q[u] = -1;
+            if (p < N) {
+                const int t = find_last_le(b.off, L, p);
+                q[u] = q0s[t] + (p - b.off[t]);
+                if constexpr (P::kVal) a[u] = as[t];
             }
-            lo = b.off[t];
-            hi = b.off[t + 1];
-            const int k = acol[t];
-            q0 = brp[k];
-            if constexpr (P::kVal) a = aval[t];
         }
-        const int q = q0 + (p - lo);
-        b.col[p] = bcol[q];
-        if constexpr (P::kVal) b.val[p] = P::mul(a, bval[q]);
+        int32_t c[UNR];
+        In v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (q[u] >= 0) {
+                c[u] = __ldg(bcol + q[u]);
+                if constexpr (P::kVal) v[u] = __ldg(bval + q[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int p = base + u * G::N + g.rank();
+            if (q[u] >= 0) {
+                b.col[p] = c[u];
+                if constexpr (P::kVal) b.val[p] = P::mul(a[u], v[u]);
+            }
+        }
     }
     g.sync();
     return N;
 }
 
 // ---------------------------------------------------------------------------
+// Where a merging round puts its output.
+//   BufSink   the other ping-pong buffer, with the new list offsets;
+//   OutSink   the row's slot in C (or C_bar) -- the last round of a numeric
+//             pass writes its single list there directly;
+//   CountSink nowhere -- the last round of the symbolic pass only counts.
+// ---------------------------------------------------------------------------
+template <class P>
+struct BufSink {
+    Buf<P> d;
+    static constexpr bool kOffsets = true;
+    __device__ __forceinline__ void put(int w, int32_t c, typename P::T v) const {
+        d.col[w] = c;
+        if constexpr (P::kVal) d.val[w] = v;
+    }
+};
+
+template <class P>
+struct OutSink {
+    int32_t *col;
+    typename P::Out *val;
+    int cap;
+    static constexpr bool kOffsets = false;
+    __device__ __forceinline__ void put(int w, int32_t c, typename P::T v) const {
+        if (w < cap) {
+            col[w] = c;
+            val[w] = P::fin(v);
+        }
+    }
+};
+
+template <class P>
+struct CountSink {
+    static constexpr bool kOffsets = false;
+    __device__ __forceinline__ void put(int, int32_t, typename P::T) const {}
+};
+
+// ---------------------------------------------------------------------------
 // One merging round: nl lists in s -> ceil(nl/2) lists in d.
 // ---------------------------------------------------------------------------
-template <class P, class G, int K>
-__device__ __forceinline__ void merge_round(const G &g, int nl, const Buf<P> s, const Buf<P> d) {
+template <class P, class G, int K, class Sink>
+__device__ __forceinline__ int merge_round(const G &g, int nl, const Buf<P> s, const Sink &sink) {
     using T = typename P::T;
     const int N = s.off[nl];
     const int np = (nl + 1) >> 1;
@@ -252,12 +316,14 @@ __device__ __forceinline__ void merge_round(const G &g, int nl, const Buf<P> s, 
                 const int mid = (l + h) >> 1;
                 if (s.col[xi + mid] <= s.col[yj + dd - 1 - mid]) l = mid + 1; else h = mid;
             }
-            if (dd == 0) {
-                // pair m -- and any empty pairs right before it -- start here
-                mfirst = m;
-                while (mfirst > 0 && s.off[2 * (mfirst - 1)] == d0) --mfirst;
-                for (int mm = mfirst; mm <= m; ++mm) d.off[mm] = 0;
-                mlast = m;
+            if constexpr (Sink::kOffsets) {
+                if (dd == 0) {
+                    // pair m -- and any empty pairs right before it -- start here
+                    mfirst = m;
+                    while (mfirst > 0 && s.off[2 * (mfirst - 1)] == d0) --mfirst;
+                    for (int mm = mfirst; mm <= m; ++mm) sink.d.off[mm] = 0;
+                    mlast = m;
+                }
             }
             yj += dd - l;
             xi += l;
@@ -288,9 +354,11 @@ __device__ __forceinline__ void merge_round(const G &g, int nl, const Buf<P> s, 
                                 xlim = s.off[2 * m + 1];
                                 yj = xlim;
                                 ylim = (2 * m + 2 <= nl) ? s.off[2 * m + 2] : xlim;
-                                d.off[m] = cnt;
-                                if (mlast < 0) mfirst = m;
-                                mlast = m;
+                                if constexpr (Sink::kOffsets) {
+                                    sink.d.off[m] = cnt;
+                                    if (mlast < 0) mfirst = m;
+                                    mlast = m;
+                                }
                                 xc = xi < xlim ? s.col[xi] : kColEnd;
                                 yc = yj < ylim ? s.col[yj] : kColEnd;
                                 if constexpr (P::kVal) {
@@ -329,61 +397,62 @@ __device__ __forceinline__ void merge_round(const G &g, int nl, const Buf<P> s, 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if ((vmask >> k) & 1u) {
-                d.col[w] = oc[k];
-                if constexpr (P::kVal) d.val[w] = ov[k];
+                sink.put(w, oc[k], ov[k]);
                 ++w;
             }
         }
-        for (int mm = mfirst; mm <= mlast; ++mm) d.off[mm] += base + ex;
+        if constexpr (Sink::kOffsets) {
+            for (int mm = mfirst; mm <= mlast; ++mm) sink.d.off[mm] += base + ex;
+        }
         base += tot;
     }
-    // pairs that start after the last element (trailing empty lists) and the end
-    for (int m = g.rank(); m < np; m += G::N)
-        if (s.off[2 * m] == N) d.off[m] = base;
-    if (g.rank() == 0) d.off[np] = base;
+    if constexpr (Sink::kOffsets) {
+        // pairs that start after the last element (trailing empty lists) and the end
+        for (int m = g.rank(); m < np; m += G::N)
+            if (s.off[2 * m] == N) sink.d.off[m] = base;
+        if (g.rank() == 0) sink.d.off[np] = base;
+    }
     g.sync();
+    return base;
 }
 
-// Whole row: multiplying phase into b0, then the accumulating phase.
-// Returns the buffer holding the result (0: b0, 1: b1) and its length.
-template <class P, class G, int K>
-__device__ __forceinline__ int brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1,
-                                       int &len) {
+// Whole row (Algorithm 1 for one i): the multiplying phase into b0, merging
+// rounds between b0 and b1 while more than two lists are left, then the last
+// round -- or, for a row of one list, a copy -- into the row's output slot
+// (the last line of Algorithm 1).  Numeric passes write C (or C_bar) at
+// out_rp[row]; every pass may record the row length in out_cnt[row].
+template <class P, class G, int K, int UNR>
+__device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1) {
     using In = typename P::In;
     const int a0 = j.arp[row];
     const int L = j.arp[row + 1] - a0;
-    multiply_phase<P, G>(g, L, j.acol + a0, static_cast<const In *>(j.aval) + a0, j.brp, j.bcol,
-                         static_cast<const In *>(j.bval), b0);
+    multiply_phase<P, G, UNR>(g, L, j.acol + a0, static_cast<const In *>(j.aval) + a0, j.brp, j.bcol,
+                              static_cast<const In *>(j.bval), b0, b1);
     Buf<P> s = b0, d = b1;
-    int which = 0, nl = L;
-    while (nl > 1) {
-        merge_round<P, G, K>(g, nl, s, d);
+    int nl = L;
+    while (nl > 2) {
+        merge_round<P, G, K>(g, nl, s, BufSink<P>{d});
         const Buf<P> t = s; s = d; d = t;
-        which ^= 1;
         nl = (nl + 1) >> 1;
     }
-    len = s.off[nl];
-    return which;
-}
-
-// Row store (Algorithm 1, last step): numeric passes copy the row to
-// out_col/out_val at out_rp[row]; every pass may record the row length.
-template <class P, class G>
-__device__ __forceinline__ void store_row(const G &g, int row, const RowJob &j, const Buf<P> &s, int len) {
+    int len;
     if constexpr (P::kVal) {
-        using Out = typename P::Out;
         const int64_t base = j.out_rp[row];
         // the row's slot: exactly nnz(C_i*) (Precise) or nprod_i (Upper)
-        const int64_t cap = j.out_rp[row + 1] - base;
-        if (len > cap) {
+        const int cap = (int)(j.out_rp[row + 1] - base);
+        const OutSink<P> out{j.out_col + base, static_cast<typename P::Out *>(j.out_val) + base, cap};
+        if (nl == 2) {
+            len = merge_round<P, G, K>(g, nl, s, out);
+        } else {
+            len = s.off[nl];
+            for (int p = g.rank(); p < len; p += G::N) out.put(p, s.col[p], s.val[p]);
+        }
+        if (len > cap || (j.exact && len != cap)) {
             if (g.rank() == 0) atomicOr(j.err, 1u);
-            len = (int)cap;
         }
-        Out *ov = static_cast<Out *>(j.out_val);
-        for (int p = g.rank(); p < len; p += G::N) {
-            j.out_col[base + p] = s.col[p];
-            ov[base + p] = P::fin(s.val[p]);
-        }
+    } else {
+        if (nl == 2) len = merge_round<P, G, K>(g, nl, s, CountSink<P>{});
+        else len = s.off[nl];
     }
     if (j.out_cnt != nullptr && g.rank() == 0) j.out_cnt[row] = len;
     g.sync();

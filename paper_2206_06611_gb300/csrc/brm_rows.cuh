@@ -15,6 +15,7 @@
 namespace brm {
 
 constexpr int kWarpK = 8;        // diagonals per thread per tile, warp kernel
+constexpr int kWarpUnr = 4;      // products gathered per thread at a time
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockThreads = 256;
 constexpr int kBlockK = 8;
@@ -24,7 +25,9 @@ constexpr int kLongK = 8;
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory bytes of one row buffer pair holding `cap` elements and
-// `lcap` lists: two value arrays, two column arrays, two offset arrays.
+// `lcap` lists: two value arrays, two column arrays, two offset arrays.  The
+// bins guarantee L <= lcap <= cap, so the spare value array can hold one A
+// value per list during the multiplying phase.
 template <class P>
 __host__ __device__ constexpr size_t pair_bytes(int cap, int lcap) {
     return (P::kVal ? align_up(2 * sizeof(typename P::T) * (size_t)cap, 16) : 0) +
@@ -49,44 +52,50 @@ __device__ __forceinline__ void carve(unsigned char *p, int cap, int lcap, Buf<P
     b1.off = b0.off + (lcap + 1);
 }
 
+static_assert(kBlockLCap <= kBlockCap, "block bin: list capacity must not exceed element capacity");
+
 template <class P, int WCAP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rows_warp(RowJob j) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) k_rows_warp(RowJob j) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int wid = threadIdx.x >> 5;
     Buf<P> b0, b1;
     carve<P>(smem + (size_t)wid * pair_bytes<P>(WCAP, WCAP), WCAP, WCAP, b0, b1);
     const WarpGrp g;
-    for (int r = blockIdx.x * kWarpsPerBlock + wid; r < j.count; r += gridDim.x * kWarpsPerBlock) {
-        const int row = j.rows[r];
-        int len;
-        const int which = brm_row<P, WarpGrp, kWarpK>(g, row, j, b0, b1, len);
-        store_row<P, WarpGrp>(g, row, j, which ? b1 : b0, len);
-    }
+    for (int r = blockIdx.x * kWarpsPerBlock + wid; r < j.count; r += gridDim.x * kWarpsPerBlock)
+        brm_row<P, WarpGrp, kWarpK, kWarpUnr>(g, j.rows[r], j, b0, b1);
 }
 
 template <class P, int BCAP, int BLCAP>
-__global__ void __launch_bounds__(kBlockThreads) k_rows_block(RowJob j) {
+__global__ void __launch_bounds__(kBlockThreads, 2) k_rows_block(RowJob j) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ws[kBlockThreads / 32 + 1];
     Buf<P> b0, b1;
     carve<P>(smem, BCAP, BLCAP, b0, b1);
     BlockGrp<kBlockThreads> g;
     g.ws = ws;
-    for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
-        const int row = j.rows[r];
-        int len;
-        const int which = brm_row<P, BlockGrp<kBlockThreads>, kBlockK>(g, row, j, b0, b1, len);
-        store_row<P, BlockGrp<kBlockThreads>>(g, row, j, which ? b1 : b0, len);
-    }
+    for (int r = blockIdx.x; r < j.count; r += gridDim.x)
+        brm_row<P, BlockGrp<kBlockThreads>, kBlockK, 4>(g, j.rows[r], j, b0, b1);
 }
 
-// Arena layout of one long row with n products and L lists (host and device
-// agree on it through this function).
+// Arena layout of one long row with n products and L lists; host and device
+// both use it.  The value arrays hold max(n, L) entries because the
+// multiplying phase parks one A value per list in the spare buffer (a row may
+// have more lists than products when many B rows are empty).
+struct LongLayout {
+    size_t val1, col0, col1, off0, off1, total;
+};
+
 template <class P>
-__host__ __device__ constexpr size_t long_row_bytes(int64_t n, int64_t L) {
-    return (P::kVal ? align_up(2 * sizeof(typename P::T) * (size_t)n, 256) : 0) +
-           align_up(2 * sizeof(int32_t) * (size_t)n, 256) + align_up(2 * sizeof(int32_t) * (size_t)(L + 1), 256);
+__host__ __device__ constexpr LongLayout long_layout(int64_t n, int64_t L) {
+    const size_t nv = (size_t)(n > L ? n : L);
+    const size_t vb = P::kVal ? align_up(sizeof(typename P::T) * nv, 256) : 0;
+    const size_t cb = align_up(sizeof(int32_t) * (size_t)n, 256);
+    const size_t ob = align_up(sizeof(int32_t) * (size_t)(L + 1), 256);
+    return LongLayout{vb, 2 * vb, 2 * vb + cb, 2 * vb + 2 * cb, 2 * vb + 2 * cb + ob, 2 * vb + 2 * cb + 2 * ob};
 }
+
+template <class P>
+__host__ __device__ constexpr size_t long_row_bytes(int64_t n, int64_t L) { return long_layout<P>(n, L).total; }
 
 template <class P>
 __global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
@@ -99,23 +108,20 @@ __global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
         const int64_t n = j.slot_nprod[r];
         const int L = j.arp[row + 1] - j.arp[row];
         unsigned char *p = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[r];
+        const LongLayout lay = long_layout<P>(n, L);
         Buf<P> b0, b1;
         if constexpr (P::kVal) {
             b0.val = reinterpret_cast<T *>(p);
-            b1.val = b0.val + n;
-            p += align_up(2 * sizeof(T) * (size_t)n, 256);
+            b1.val = reinterpret_cast<T *>(p + lay.val1);
         } else {
             b0.val = nullptr;
             b1.val = nullptr;
         }
-        b0.col = reinterpret_cast<int32_t *>(p);
-        b1.col = b0.col + n;
-        p += align_up(2 * sizeof(int32_t) * (size_t)n, 256);
-        b0.off = reinterpret_cast<int32_t *>(p);
-        b1.off = b0.off + (L + 1);
-        int len;
-        const int which = brm_row<P, BlockGrp<kLongThreads>, kLongK>(g, row, j, b0, b1, len);
-        store_row<P, BlockGrp<kLongThreads>>(g, row, j, which ? b1 : b0, len);
+        b0.col = reinterpret_cast<int32_t *>(p + lay.col0);
+        b1.col = reinterpret_cast<int32_t *>(p + lay.col1);
+        b0.off = reinterpret_cast<int32_t *>(p + lay.off0);
+        b1.off = reinterpret_cast<int32_t *>(p + lay.off1);
+        brm_row<P, BlockGrp<kLongThreads>, kLongK, 4>(g, row, j, b0, b1);
     }
 }
 
