@@ -166,6 +166,42 @@ int brm_spgemm_precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
 int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
                      const brm_options *opts, const brm_allocator *alloc, void *stream);
 
+/*
+ * Numeric pass of BRMerge-Precise that allocates no device memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or an allocator of their own -- an application that has given
+ * all device memory to its own pool, a latency-bound loop that must not take
+ * the implicit synchronisation of an allocation, or a plug-in that may only
+ * touch the buffers it is handed.  The caller passes C's row pointer (for
+ * example from brm_spgemm_symbolic on the same A and B) and C's column and
+ * value arrays, sized C_row_ptr[A.rows] entries; every row of C is written
+ * into its slot, columns strictly ascending, with the same values as
+ * brm_spgemm_precise gives.
+ *   A, B        inputs as for brm_spgemm_precise (values required).
+ *   C_row_ptr   device int64[A.rows + 1], read only; must be the exact row
+ *               pointer of A * B (a row whose merged length differs from its
+ *               slot makes the call fail with BRM_ERR_INVALID, and nothing is
+ *               written outside the slots).
+ *   C_col_idx   device int32[nnz(C)], written.
+ *   C_val       device float/double[nnz(C)] (A's dtype), written.
+ *   opts        validate, compensated, warp_max_nprod and block_max_nprod as
+ *               elsewhere; arena_bytes is ignored.
+ * Limits: A.rows <= 2^20, and every row must fit a shared-memory bin
+ * (nprod_i <= block_max_nprod and at most 1024 lists); otherwise the call
+ * returns BRM_ERR_OVERFLOW with a message and writes nothing into C.
+ * Workspace: a fixed 8 MiB device array inside the library (held on every
+ * GPU that loads it until the process exits) instead of allocations.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress)
+ * with the device current, so make the first call on each device before any
+ * stream capture starts.  Every call reuses the same array and clears the
+ * parts that must start at zero; calls that overlap on the GPU (on different
+ * streams or from different host threads) race on it and must be avoided.
+ * Synchronises the stream twice (bins; the row-length check), three times
+ * with validate.
+ */
+int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, int32_t *C_col_idx,
+                               void *C_val, const brm_options *opts, void *stream);
+
 /* Frees the arrays of a brm_csr_out with the given allocator and zeroes it. */
 void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);
 

@@ -94,7 +94,9 @@ def load(build_if_needed: bool = True):
     lib.brm_csr_out_free.argtypes = [pout, pal, P]
     lib.brm_csr_out_free.restype = None
     lib.brm_row_nprod.argtypes = [pcsr, pcsr, P, P, P, P, P]
-    for f in (lib.brm_spgemm_symbolic, lib.brm_spgemm_precise, lib.brm_spgemm_upper, lib.brm_row_nprod):
+    lib.brm_spgemm_numeric_noalloc.argtypes = [pcsr, pcsr, P, P, P, popt, P]
+    for f in (lib.brm_spgemm_symbolic, lib.brm_spgemm_precise, lib.brm_spgemm_upper, lib.brm_row_nprod,
+              lib.brm_spgemm_numeric_noalloc):
         f.restype = ctypes.c_int
     lib.brm_trace_enable.argtypes = [ctypes.c_int]
     lib.brm_trace_enable.restype = ctypes.c_int
@@ -281,6 +283,27 @@ def brm_spgemm_symbolic(A: DeviceCSR, B: DeviceCSR, *, validate=False, stream=No
                                    ctypes.byref(nnz), ctypes.byref(o), ctypes.byref(_allocator().struct),
                                    _stream(stream)))
     return rp, int(nnz.value)
+
+
+def brm_spgemm_numeric_noalloc(A: DeviceCSR, B: DeviceCSR, C_rp, C_col, C_val, *, compensated=False,
+                               validate=False, stream=None, **opts) -> DeviceCSR:
+    """Numeric pass into caller-provided C arrays; the library allocates
+    nothing (its workspace is a fixed array inside libbrm).  C_rp is the int64
+    row pointer of A*B (e.g. from brm_spgemm_symbolic); C_col (int32) and C_val
+    (A's dtype) hold C_rp[-1] entries and are overwritten."""
+    import torch
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    if C_rp.dtype != torch.int64 or C_col.dtype != torch.int32 or C_val.dtype != A.val.dtype:
+        raise TypeError("C_rp must be int64, C_col int32 and C_val of A's value dtype")
+    for t in (C_rp, C_col, C_val):
+        if not t.is_cuda or not t.is_contiguous():
+            raise TypeError("C arrays must be contiguous CUDA tensors")
+    o = options(validate=validate, compensated=compensated, **opts)
+    _check(lib.brm_spgemm_numeric_noalloc(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(C_rp.data_ptr()),
+                                          ctypes.c_void_p(C_col.data_ptr()), ctypes.c_void_p(C_val.data_ptr()),
+                                          ctypes.byref(o), _stream(stream)))
+    return DeviceCSR(A.rows, B.cols, C_rp, C_col, C_val)
 
 
 def brm_row_nprod(A: DeviceCSR, B: DeviceCSR, *, stream=None):

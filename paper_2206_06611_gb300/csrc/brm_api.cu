@@ -634,3 +634,124 @@ const char *brm_trace_phase_name(int i) { return (i >= 0 && i < kNumPhases) ? kP
 int64_t brm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Numeric phase without any device allocation.
+//
+// Some callers may not allocate device memory at all: a host application that
+// has handed the whole GPU to its own memory pool, a real-time loop in which
+// the implicit synchronisation of cudaMalloc/cudaFree is not acceptable, or a
+// plug-in that runs inside someone else's process and may only touch the
+// buffers it was given.  For them the numeric pass of BRMerge-Precise is
+// offered with its workspace (the binning statistics, the per-bin row lists
+// and the row-length flag) in the fixed array below instead of in allocated
+// memory.  The array lives in every GPU that loads the library until the
+// process exits; host code must not use its name as a device address and
+// gets the address through cudaGetSymbolAddress once per device.
+// ---------------------------------------------------------------------------
+namespace brm {
+namespace {
+
+constexpr int64_t kNoallocMaxRows = int64_t(1) << 20;
+constexpr size_t kNoallocHeader = 512;                      // BinStats, then the flag at 256
+constexpr size_t kNoallocBytes = kNoallocHeader + 2 * sizeof(int32_t) * (size_t)kNoallocMaxRows;
+static_assert(sizeof(BinStats) <= 256, "statistics must fit the first 256 bytes");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device, with that device current).
+int noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    BRM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(BRM_ERR_INVALID, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        BRM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return BRM_OK;
+}
+
+int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, int32_t *C_col, void *C_val,
+                    const brm_options *opts, cudaStream_t st) {
+    int rc = check_pair(A, B, true);
+    if (rc) return rc;
+    if (A->rows > kNoallocMaxRows)
+        return fail(BRM_ERR_OVERFLOW, "A has %lld rows; brm_spgemm_numeric_noalloc handles at most %lld",
+                    (long long)A->rows, (long long)kNoallocMaxRows);
+    if (!C_row_ptr) return fail(BRM_ERR_INVALID, "C_row_ptr is NULL");
+    const brm_options o = resolve(opts);
+    const int64_t m = A->rows;
+    unsigned char *scr = nullptr;
+    if ((rc = noalloc_scratch(&scr))) return rc;
+    BinStats *stats = reinterpret_cast<BinStats *>(scr);
+    unsigned int *err = reinterpret_cast<unsigned int *>(scr + 256);
+    int32_t *rows_warp = reinterpret_cast<int32_t *>(scr + kNoallocHeader);
+    int32_t *rows_block = rows_warp + kNoallocMaxRows;
+    // the array keeps the previous call's contents: zero what is accumulated
+    BRM_CUDA(cudaMemsetAsync(scr, 0, kNoallocHeader, st));
+    BinStats h{};
+    if (o.validate) {
+        BRM_CUDA(launch_validate(A->rows, A->cols, A->nnz, A->row_ptr, A->col_idx, stats, st));
+        BRM_CUDA(launch_validate(B->rows, B->cols, B->nnz, B->row_ptr, B->col_idx, stats, st));
+        BRM_CUDA(cudaMemcpyAsync(&h, stats, sizeof h, cudaMemcpyDeviceToHost, st));
+        BRM_CUDA(cudaStreamSynchronize(st));
+        if (h.bad) return fail(BRM_ERR_INVALID, "malformed CSR input (row_ptr or column order/range)");
+    }
+    if (m == 0) return BRM_OK;
+    BinArgs a{};
+    a.m = m;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.brp = B->row_ptr;
+    a.warp_cap = o.warp_max_nprod;
+    a.block_cap = o.block_max_nprod;
+    a.block_lcap = kBlockLCap;
+    a.bin_rows[kBinWarp] = rows_warp;
+    a.bin_rows[kBinBlock] = rows_block;   // long rows are only counted
+    a.st = stats;
+    BRM_CUDA(launch_bin(a, st));
+    BRM_CUDA(cudaMemcpyAsync(&h, stats, sizeof h, cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    if (h.count[kBinLong] > 0)
+        return fail(BRM_ERR_OVERFLOW,
+                    "%llu rows have more than %d products or %d lists; brm_spgemm_numeric_noalloc only merges rows "
+                    "that fit in shared memory",
+                    h.count[kBinLong], o.block_max_nprod, kBlockLCap);
+    RowJob j = base_job(A, B);
+    j.out_rp = C_row_ptr;
+    j.out_col = C_col;
+    j.out_val = C_val;
+    j.err = err;
+    j.exact = 1;
+    const VKind v = value_kind(A, o);
+    int32_t *lists[2] = {rows_warp, rows_block};
+    for (int b = kBinWarp; b <= kBinBlock; ++b) {
+        RowJob jb = j;
+        jb.rows = lists[b - kBinWarp];
+        jb.count = (int32_t)h.count[b];
+        if (jb.count == 0) continue;
+        BRM_CUDA(launch_rows(v, b, jb, st));
+    }
+    unsigned int flag = 0;
+    BRM_CUDA(cudaMemcpyAsync(&flag, err, sizeof flag, cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    if (flag) return fail(BRM_ERR_INVALID, "a numeric row length disagrees with C_row_ptr");
+    return BRM_OK;
+}
+
+}  // namespace
+}  // namespace brm
+
+extern "C" int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr,
+                                          int32_t *C_col_idx, void *C_val, const brm_options *opts, void *stream) {
+    brm::g_err.clear();
+    return brm::numeric_noalloc(A, B, C_row_ptr, C_col_idx, C_val, opts, static_cast<cudaStream_t>(stream));
+}
