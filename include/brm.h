@@ -101,8 +101,14 @@ typedef struct {
  *                  elements in the merge tree is TwoSum-compensated (Knuth,
  *                  TAOCP vol. 2, 4.2.2): each element carries a float
  *                  running error, the stored value is sum + error.
- *   warp_max_nprod rows with 0 < nprod <= this (and <= as many lists) are
- *                  merged by one warp in shared memory (at most 512).
+ *   reg_max_nprod  rows with 0 < nprod <= this (at most 1024; 0 = 1024,
+ *                  negative = none) and at most nprod/4 lists are merged with
+ *                  their keys in registers by 1..32 threads per row, when B
+ *                  has few enough columns to pack a column and a position into
+ *                  32 bits (2^27 - 1 for rows of <= 32 products, halving per
+ *                  doubling of the row size);
+ *   warp_max_nprod other rows with 0 < nprod <= this (and <= as many lists)
+ *                  are merged by one warp in shared memory (at most 256).
  *   block_max_nprod rows up to this many products are merged by one thread
  *                  block in shared memory; longer rows use the device-memory
  *                  ping-pong arena (bounded by the kernel's shared memory).
@@ -115,6 +121,7 @@ typedef struct {
     int32_t compensated;
     int32_t warp_max_nprod;
     int32_t block_max_nprod;
+    int32_t reg_max_nprod;
     size_t arena_bytes;
 } brm_options;
 
@@ -189,7 +196,7 @@ int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
  * Limits: A.rows <= 2^20, and every row must fit a shared-memory bin
  * (nprod_i <= block_max_nprod and at most 1024 lists); otherwise the call
  * returns BRM_ERR_OVERFLOW with a message and writes nothing into C.
- * Workspace: a fixed 8 MiB device array inside the library (held on every
+ * Workspace: a fixed 5 MiB device array inside the library (held on every
  * GPU that loads it until the process exits) instead of allocations.  The
  * first call on a device looks up that array's address (cudaGetSymbolAddress)
  * with the device current, so make the first call on each device before any
@@ -201,6 +208,29 @@ int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
  */
 int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, int32_t *C_col_idx,
                                void *C_val, const brm_options *opts, void *stream);
+
+/*
+ * Backward pass of C = A * B for a scalar loss with dLoss/dC = G given on C's
+ * pattern (the differentiable form; the paper's method is the forward pass,
+ * Eq. 2):
+ *   dA_ik = sum_{j in B_k*} G_ij * B_kj           for every stored (i, k) of A,
+ *   dB_kj = sum_{i : k in A_i*} A_ik * G_ij      for every stored (k, j) of B,
+ * i.e. (G * B^T) masked to A's pattern and (A^T * G) masked to B's pattern.
+ *   A, B         the forward inputs (values required, same dtype).
+ *   C_row_ptr,   device int64[A.rows + 1] and int32[nnz(C)]: the pattern of C
+ *   C_col_idx    as returned by brm_spgemm_precise / brm_spgemm_upper (every
+ *                column of every B_k*, k in A_i*, must be present in row i).
+ *   dC           device values of G on C's pattern (A's dtype).
+ *   dA_val       device, A.nnz values, written (NULL: not computed).
+ *   dB_val       device, B.nnz values, overwritten (NULL: not computed).
+ * dA is summed sequentially per entry (deterministic); dB is accumulated with
+ * atomic additions, so its rounding may differ between runs.  Returns
+ * BRM_ERR_INVALID if C's pattern misses a column.  Synchronises the stream
+ * once.  opts is unused (may be NULL); alloc provides one 4-byte flag.
+ */
+int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, const int32_t *C_col_idx,
+                        const void *dC, void *dA_val, void *dB_val, const brm_options *opts,
+                        const brm_allocator *alloc, void *stream);
 
 /* Frees the arrays of a brm_csr_out with the given allocator and zeroes it. */
 void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);
@@ -220,8 +250,9 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
  * time of each part of the computation).  With tracing on, every later call
  * records CUDA events on its stream around each kernel phase; the elapsed
  * device times are added per phase when the call returns.  Phases, in order:
- * validate, bin, symbolic_warp, symbolic_block, symbolic_long, scan,
- * numeric_warp, numeric_block, numeric_long, compact.  Not thread-safe across
+ * validate, bin, symbolic_reg, symbolic_warp, symbolic_block, symbolic_long,
+ * scan, numeric_reg, numeric_warp, numeric_block, numeric_long, compact,
+ * backward.  Not thread-safe across
  * concurrent calls from several host threads.
  *   brm_trace_enable      on != 0 enables; returns the previous setting.
  *   brm_trace_reset       zeroes the accumulated times and launch counts.

@@ -51,7 +51,7 @@ class brm_allocator(ctypes.Structure):
 class brm_options(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("compensated", ctypes.c_int32),
                 ("warp_max_nprod", ctypes.c_int32), ("block_max_nprod", ctypes.c_int32),
-                ("arena_bytes", ctypes.c_size_t)]
+                ("reg_max_nprod", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t)]
 
 
 class BrmError(RuntimeError):
@@ -95,6 +95,8 @@ def load(build_if_needed: bool = True):
     lib.brm_csr_out_free.restype = None
     lib.brm_row_nprod.argtypes = [pcsr, pcsr, P, P, P, P, P]
     lib.brm_spgemm_numeric_noalloc.argtypes = [pcsr, pcsr, P, P, P, popt, P]
+    lib.brm_spgemm_backward.argtypes = [pcsr, pcsr, P, P, P, P, P, popt, pal, P]
+    lib.brm_spgemm_backward.restype = ctypes.c_int
     for f in (lib.brm_spgemm_symbolic, lib.brm_spgemm_precise, lib.brm_spgemm_upper, lib.brm_row_nprod,
               lib.brm_spgemm_numeric_noalloc):
         f.restype = ctypes.c_int
@@ -224,7 +226,8 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, arena_bytes=0) -> brm_options:
+def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
+            arena_bytes=0) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -233,6 +236,8 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
         o.warp_max_nprod = warp_max_nprod
     if block_max_nprod:
         o.block_max_nprod = block_max_nprod
+    if reg_max_nprod:
+        o.reg_max_nprod = reg_max_nprod
     o.arena_bytes = arena_bytes
     return o
 
@@ -304,6 +309,69 @@ def brm_spgemm_numeric_noalloc(A: DeviceCSR, B: DeviceCSR, C_rp, C_col, C_val, *
                                           ctypes.c_void_p(C_col.data_ptr()), ctypes.c_void_p(C_val.data_ptr()),
                                           ctypes.byref(o), _stream(stream)))
     return DeviceCSR(A.rows, B.cols, C_rp, C_col, C_val)
+
+
+def brm_spgemm_backward(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, dC, want_da=True, want_db=True, stream=None):
+    """(dA on A's pattern, dB on B's pattern) of a loss with dLoss/dC = dC on
+    C's pattern; either is None when not wanted."""
+    import torch
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    if dC.dtype != A.val.dtype or not dC.is_cuda or not dC.is_contiguous() or dC.numel() != C.nnz:
+        raise TypeError("dC must be a contiguous CUDA tensor of C's nnz values in A's dtype")
+    dA = torch.empty_like(A.val) if want_da else None
+    dB = torch.empty_like(B.val) if want_db else None
+    _check(lib.brm_spgemm_backward(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(C.rp.data_ptr()),
+                                   ctypes.c_void_p(C.col.data_ptr() if C.nnz else None),
+                                   ctypes.c_void_p(dC.data_ptr() if C.nnz else None),
+                                   ctypes.c_void_p(dA.data_ptr() if dA is not None and A.nnz else None),
+                                   ctypes.c_void_p(dB.data_ptr() if dB is not None and B.nnz else None),
+                                   None, ctypes.byref(_allocator().struct), _stream(stream)))
+    return dA, dB
+
+
+def _spgemm_fn():
+    import torch
+
+    class _SpGEMM(torch.autograd.Function):
+        """C.val = (A * B).val with the hand-written masked backward."""
+
+        @staticmethod
+        def forward(ctx, a_val, b_val, A, B, method, opts):
+            dA = DeviceCSR(A.rows, A.cols, A.rp, A.col, a_val.detach())
+            dB = DeviceCSR(B.rows, B.cols, B.rp, B.col, b_val.detach())
+            f = brm_spgemm_precise if method == "precise" else brm_spgemm_upper
+            C = f(dA, dB, **opts)
+            ctx.save_for_backward(a_val.detach(), b_val.detach(), C.rp, C.col)
+            ctx.shapes = (A, B)
+            ctx.mark_non_differentiable(C.rp, C.col)
+            return C.val, C.rp, C.col
+
+        @staticmethod
+        def backward(ctx, g_val, g_rp, g_col):
+            a_val, b_val, crp, ccol = ctx.saved_tensors
+            A, B = ctx.shapes
+            dA = DeviceCSR(A.rows, A.cols, A.rp, A.col, a_val)
+            dB = DeviceCSR(B.rows, B.cols, B.rp, B.col, b_val)
+            C = DeviceCSR(A.rows, B.cols, crp, ccol, None)
+            ga, gb = brm_spgemm_backward(dA, dB, C, g_val.contiguous(), want_da=ctx.needs_input_grad[0],
+                                         want_db=ctx.needs_input_grad[1])
+            return ga, gb, None, None, None, None
+
+    return _SpGEMM
+
+
+_SPGEMM = None
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, method: str = "precise", **opts) -> DeviceCSR:
+    """C = A*B whose values are differentiable with respect to A.val and
+    B.val (torch autograd); the backward pass is brm_spgemm_backward."""
+    global _SPGEMM
+    if _SPGEMM is None:
+        _SPGEMM = _spgemm_fn()
+    val, rp, col = _SPGEMM.apply(A.val, B.val, A, B, method, opts)
+    return DeviceCSR(A.rows, B.cols, rp, col, val)
 
 
 def brm_row_nprod(A: DeviceCSR, B: DeviceCSR, *, stream=None):

@@ -176,13 +176,25 @@ brm_options resolve(const brm_options *o) {
     if (r.warp_max_nprod <= 0 || r.warp_max_nprod > kWarpCap) r.warp_max_nprod = kWarpCap;
     if (r.block_max_nprod <= 0 || r.block_max_nprod > kBlockCap) r.block_max_nprod = kBlockCap;
     if (r.block_max_nprod < r.warp_max_nprod) r.block_max_nprod = r.warp_max_nprod;
+    if (r.reg_max_nprod == 0 || r.reg_max_nprod > kRegMaxNprod) r.reg_max_nprod = kRegMaxNprod;
+    if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
+}
+
+// Largest threads-per-row of a register bin usable for this product: its
+// capacity within reg_max_nprod and B's column count packable into its keys.
+int reg_max_tpr(const brm_options &o, const brm_csr *B) {
+    int best = 0;
+    for (int tpr = 1; tpr <= kRegMaxTpr; tpr <<= 1)
+        if (kRegE * tpr <= o.reg_max_nprod && B->cols <= reg_col_limit(tpr)) best = tpr;
+    return best;
 }
 
 // Result of the binning step.
 struct Plan {
     BinStats stats{};
-    int32_t *bin_rows[kNumBins] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *rows = nullptr;            // device: the rows of every bin, bin after bin
+    int64_t base[kNumBins] = {};        // where bin b starts in rows
     int64_t *long_nprod = nullptr;      // device, per long slot (binning order)
     int32_t *long_L = nullptr;
     int32_t *long_rows_s = nullptr;     // device, long rows sorted by nprod (descending)
@@ -214,43 +226,59 @@ int validate_inputs(Mem &mem, const brm_csr *A, const brm_csr *B) {
 int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o, Plan &pl, int64_t *nprod,
               int64_t *row_cnt) {
     const int64_t m = A->rows;
+    const size_t m1 = (size_t)std::max<int64_t>(m, 1);
     BinStats *st;
     int rc = get(mem, st, 1, "bin statistics");
     if (rc) return rc;
     BRM_CUDA(cudaMemsetAsync(st, 0, sizeof(BinStats), mem.st));
-    for (int b = kBinWarp; b < kNumBins; ++b)
-        if ((rc = get(mem, pl.bin_rows[b], (size_t)std::max<int64_t>(m, 1), "bin row list"))) return rc;
-    if ((rc = get(mem, pl.long_nprod, (size_t)std::max<int64_t>(m, 1), "long-row sizes"))) return rc;
-    if ((rc = get(mem, pl.long_L, (size_t)std::max<int64_t>(m, 1), "long-row list counts"))) return rc;
+    uint8_t *bin_of;
+    if ((rc = get(mem, bin_of, m1, "row bins"))) return rc;
+    if ((rc = get(mem, pl.rows, m1, "bin row lists"))) return rc;
+    if (!nprod && (rc = get(mem, nprod, m1, "row nprod"))) return rc;
     BinArgs a{};
     a.m = m;
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.brp = B->row_ptr;
+    a.reg_max_tpr = reg_max_tpr(o, B);
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;
     a.nprod = nprod;
-    for (int b = 0; b < kNumBins; ++b) a.bin_rows[b] = pl.bin_rows[b];
-    a.long_nprod = pl.long_nprod;
-    a.long_L = pl.long_L;
+    a.bin_of = bin_of;
     a.row_cnt = row_cnt;
     a.st = st;
+    a.rows = pl.rows;
     {
         PhaseScope ps(kPhBin, mem.st);
         BRM_CUDA(launch_bin(a, mem.st));
     }
     BRM_CUDA(cudaMemcpyAsync(&pl.stats, st, sizeof(BinStats), cudaMemcpyDeviceToHost, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));
-    mem.free_one(st);
     if (pl.stats.max_nprod >= (unsigned long long)INT32_MAX)
         return fail(BRM_ERR_OVERFLOW, "a row has %llu intermediate products (limit 2^31-1)", pl.stats.max_nprod);
+    int64_t off = 0;
+    for (int b = 0; b < kNumBins; ++b) {
+        pl.base[b] = a.base[b] = off;
+        if (b != kBinEmpty) off += (int64_t)pl.stats.count[b];
+    }
     const int64_t nl = (int64_t)pl.stats.count[kBinLong];
+    if (nl > 0) {
+        if ((rc = get(mem, pl.long_nprod, nl, "long-row sizes"))) return rc;
+        if ((rc = get(mem, pl.long_L, nl, "long-row list counts"))) return rc;
+        a.long_nprod = pl.long_nprod;
+        a.long_L = pl.long_L;
+    }
+    {
+        PhaseScope ps(kPhBin, mem.st);
+        BRM_CUDA(launch_bin_scatter(a, mem.st));
+    }
+    mem.free_one(st);   // stream-ordered: released after the scatter
     if (nl > 0) {
         std::vector<int32_t> rows(nl), Ls(nl);
         std::vector<int64_t> np(nl);
-        BRM_CUDA(cudaMemcpyAsync(rows.data(), pl.bin_rows[kBinLong], nl * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                 mem.st));
+        BRM_CUDA(cudaMemcpyAsync(rows.data(), pl.rows + pl.base[kBinLong], nl * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaMemcpyAsync(np.data(), pl.long_nprod, nl * sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaMemcpyAsync(Ls.data(), pl.long_L, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaStreamSynchronize(mem.st));
@@ -279,12 +307,13 @@ int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o
 
 // One BRMerge pass (symbolic or numeric) over all bins.
 int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
-    for (int b = kBinWarp; b <= kBinBlock; ++b) {
+    for (int b = kBinReg0; b <= kBinBlock; ++b) {
         RowJob jb = j;
-        jb.rows = pl.bin_rows[b];
+        jb.rows = pl.rows + pl.base[b];
         jb.count = (int32_t)pl.stats.count[b];
         if (jb.count == 0) continue;
-        PhaseScope ps((v == kIdx ? kPhSymWarp : kPhNumWarp) + (b - kBinWarp), mem.st);
+        const int ph = b < kBinWarp ? kPhSymReg : kPhSymWarp + (b - kBinWarp);
+        PhaseScope ps(v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg), mem.st);
         BRM_CUDA(launch_rows(v, b, jb, mem.st));
     }
     const int64_t nl = (int64_t)pl.long_rows_h.size();
@@ -518,6 +547,7 @@ void brm_options_default(brm_options *o) {
     o->compensated = 0;
     o->warp_max_nprod = kWarpCap;
     o->block_max_nprod = kBlockCap;
+    o->reg_max_nprod = kRegMaxNprod;
     o->arena_bytes = 0;
 }
 
@@ -556,6 +586,48 @@ int brm_spgemm_symbolic(const brm_csr *A, const brm_csr *B, int64_t *C_row_ptr, 
     return rc;
 }
 
+int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, const int32_t *C_col_idx,
+                        const void *dC, void *dA_val, void *dB_val, const brm_options *opts,
+                        const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    (void)opts;
+    int rc = check_pair(A, B, true);
+    if (rc) return rc;
+    if (!C_row_ptr || (A->rows > 0 && (!C_col_idx || !dC)))
+        return fail(BRM_ERR_INVALID, "C_row_ptr, C_col_idx and dC must not be NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Mem mem(alloc, st);
+    unsigned int *err;
+    if ((rc = get(mem, err, 1, "error flag"))) return rc;
+    BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    const size_t vb = value_bytes(A->dtype);
+    if (dB_val && B->nnz > 0) BRM_CUDA(cudaMemsetAsync(dB_val, 0, (size_t)B->nnz * vb, st));
+    BackwardArgs a{};
+    a.m = A->rows;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.aval = A->val;
+    a.brp = B->row_ptr;
+    a.bcol = B->col_idx;
+    a.bval = B->val;
+    a.crp = C_row_ptr;
+    a.ccol = C_col_idx;
+    a.dC = dC;
+    a.dA = dA_val;
+    a.dB = dB_val;
+    a.err = err;
+    {
+        PhaseScope ps(kPhBackward, st);
+        BRM_CUDA(launch_backward(a, A->dtype == BRM_F64, st));
+    }
+    unsigned int h = 0;
+    BRM_CUDA(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    g_trace.flush();
+    if (h) return fail(BRM_ERR_INVALID, "C's pattern does not contain every column of A * B");
+    return BRM_OK;
+}
+
 void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream) {
     if (!C) return;
     Mem mem(alloc, static_cast<cudaStream_t>(stream));
@@ -581,6 +653,7 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.brp = B->row_ptr;
+    a.reg_max_tpr = 0;
     a.warp_cap = kWarpCap;
     a.block_cap = kBlockCap;
     a.block_lcap = kBlockLCap;
@@ -601,8 +674,8 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
 }
 
 static const char *kPhaseNames[kNumPhases] = {
-    "validate", "bin", "symbolic_warp", "symbolic_block", "symbolic_long", "scan",
-    "numeric_warp", "numeric_block", "numeric_long", "compact"};
+    "validate", "bin", "symbolic_reg", "symbolic_warp", "symbolic_block", "symbolic_long", "scan",
+    "numeric_reg", "numeric_warp", "numeric_block", "numeric_long", "compact", "backward"};
 
 int brm_trace_enable(int on) {
     const int was = g_trace.on ? 1 : 0;
@@ -654,7 +727,8 @@ namespace {
 
 constexpr int64_t kNoallocMaxRows = int64_t(1) << 20;
 constexpr size_t kNoallocHeader = 512;                      // BinStats, then the flag at 256
-constexpr size_t kNoallocBytes = kNoallocHeader + 2 * sizeof(int32_t) * (size_t)kNoallocMaxRows;
+// header, then one bin byte per row, then the rows of all bins (int32 each)
+constexpr size_t kNoallocBytes = kNoallocHeader + (1 + sizeof(int32_t)) * (size_t)kNoallocMaxRows;
 static_assert(sizeof(BinStats) <= 256, "statistics must fit the first 256 bytes");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
@@ -693,8 +767,8 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     if ((rc = noalloc_scratch(&scr))) return rc;
     BinStats *stats = reinterpret_cast<BinStats *>(scr);
     unsigned int *err = reinterpret_cast<unsigned int *>(scr + 256);
-    int32_t *rows_warp = reinterpret_cast<int32_t *>(scr + kNoallocHeader);
-    int32_t *rows_block = rows_warp + kNoallocMaxRows;
+    uint8_t *bin_of = scr + kNoallocHeader;
+    int32_t *rows = reinterpret_cast<int32_t *>(scr + kNoallocHeader + kNoallocMaxRows);
     // the array keeps the previous call's contents: zero what is accumulated
     BRM_CUDA(cudaMemsetAsync(scr, 0, kNoallocHeader, st));
     BinStats h{};
@@ -711,12 +785,13 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.brp = B->row_ptr;
+    a.reg_max_tpr = reg_max_tpr(o, B);
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;
-    a.bin_rows[kBinWarp] = rows_warp;
-    a.bin_rows[kBinBlock] = rows_block;   // long rows are only counted
+    a.bin_of = bin_of;
     a.st = stats;
+    a.rows = rows;
     BRM_CUDA(launch_bin(a, st));
     BRM_CUDA(cudaMemcpyAsync(&h, stats, sizeof h, cudaMemcpyDeviceToHost, st));
     BRM_CUDA(cudaStreamSynchronize(st));
@@ -725,6 +800,12 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
                     "%llu rows have more than %d products or %d lists; brm_spgemm_numeric_noalloc only merges rows "
                     "that fit in shared memory",
                     h.count[kBinLong], o.block_max_nprod, kBlockLCap);
+    int64_t off = 0;
+    for (int b = 0; b < kNumBins; ++b) {
+        a.base[b] = off;
+        if (b != kBinEmpty) off += (int64_t)h.count[b];
+    }
+    BRM_CUDA(launch_bin_scatter(a, st));
     RowJob j = base_job(A, B);
     j.out_rp = C_row_ptr;
     j.out_col = C_col;
@@ -732,10 +813,9 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     j.err = err;
     j.exact = 1;
     const VKind v = value_kind(A, o);
-    int32_t *lists[2] = {rows_warp, rows_block};
-    for (int b = kBinWarp; b <= kBinBlock; ++b) {
+    for (int b = kBinReg0; b <= kBinBlock; ++b) {
         RowJob jb = j;
-        jb.rows = lists[b - kBinWarp];
+        jb.rows = rows + a.base[b];
         jb.count = (int32_t)h.count[b];
         if (jb.count == 0) continue;
         BRM_CUDA(launch_rows(v, b, jb, st));

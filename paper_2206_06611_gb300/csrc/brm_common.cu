@@ -26,8 +26,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // list count L_i = |A_i*|.  The paper then splits rows statically into p
 // groups of equal nprod for p CPU threads (Section III-D); on the GPU rows are
 // instead sorted into bins by size, each bin served by a kernel whose thread
-// group and buffer location fit that size.  Row lists per bin are appended
-// with warp-aggregated atomics.
+// group and buffer location fit that size.  This pass classifies the rows and
+// counts the bins (warp-aggregated atomics); k_bin_scatter then lists them.
 // ---------------------------------------------------------------------------
 __global__ void k_bin(BinArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,29 +41,22 @@ __global__ void k_bin(BinArgs a) {
             const int k = a.acol[p];
             np += a.brp[k + 1] - a.brp[k];
         }
+        // threads per row a register bin would need: enough for the products
+        // (32 per thread) and for the lists (8 per thread)
+        const int64_t need = max((np + kRegE - 1) / kRegE, (int64_t)(L + kRegListsPerThread - 1) / kRegListsPerThread);
         if (np == 0) bin = kBinEmpty;
+        else if (need <= a.reg_max_tpr) bin = kBinReg0 + (need <= 1 ? 0 : 32 - __clz((int)need - 1));
         else if (np <= a.warp_cap && L <= a.warp_cap) bin = kBinWarp;
         else if (np <= a.block_cap && L <= a.block_lcap) bin = kBinBlock;
         else bin = kBinLong;
         if (a.nprod) a.nprod[i] = np;
+        if (a.bin_of) a.bin_of[i] = (uint8_t)bin;
         if (bin == kBinEmpty && a.row_cnt) a.row_cnt[i] = 0;
     }
 #pragma unroll
     for (int b = 0; b < kNumBins; ++b) {
         const unsigned mask = __ballot_sync(kFull, bin == b);
-        if (mask == 0u) continue;
-        const int leader = __ffs(mask) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(&a.st->count[b], (unsigned long long)__popc(mask));
-        base = __shfl_sync(kFull, base, leader);
-        if (bin == b && b != kBinEmpty && a.bin_rows[b] != nullptr) {
-            const unsigned long long slot = base + __popc(mask & lanemask_lt());
-            a.bin_rows[b][slot] = (int32_t)i;
-            if (b == kBinLong && a.long_nprod) {
-                a.long_nprod[slot] = np;
-                a.long_L[slot] = L;
-            }
-        }
+        if (mask != 0u && lane == __ffs(mask) - 1) atomicAdd(&a.st->count[b], (unsigned long long)__popc(mask));
     }
     unsigned long long sum = (unsigned long long)np, mx = (unsigned long long)np, ml = (unsigned long long)L;
 #pragma unroll
@@ -76,6 +69,31 @@ __global__ void k_bin(BinArgs a) {
         if (sum) atomicAdd(&a.st->total_nprod, sum);
         atomicMax(&a.st->max_nprod, mx);
         atomicMax(&a.st->max_L, ml);
+    }
+}
+
+// Second pass: every non-empty row appends itself to its bin's segment of
+// a.rows (warp-aggregated atomics on the bin's cursor).
+__global__ void k_bin_scatter(BinArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int bin = i < a.m ? (int)a.bin_of[i] : -1;
+#pragma unroll
+    for (int b = kBinReg0; b < kNumBins; ++b) {
+        const unsigned mask = __ballot_sync(kFull, bin == b);
+        if (mask == 0u) continue;
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&a.st->cursor[b], (unsigned long long)__popc(mask));
+        base = __shfl_sync(kFull, base, leader);
+        if (bin == b) {
+            const int64_t slot = (int64_t)base + __popc(mask & lanemask_lt());
+            a.rows[a.base[b] + slot] = (int32_t)i;
+            if (b == kBinLong && a.long_nprod) {
+                a.long_nprod[slot] = a.nprod[i];
+                a.long_L[slot] = a.arp[i + 1] - a.arp[i];
+            }
+        }
     }
 }
 
@@ -217,6 +235,15 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t st) {
     const int T = 256;
     const int64_t grid = (a.m + T - 1) / T;
     k_bin<<<(unsigned)grid, T, 0, st>>>(a);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st) {
+    if (a.m <= 0) return cudaSuccess;
+    const int T = 256;
+    const int64_t grid = (a.m + T - 1) / T;
+    k_bin_scatter<<<(unsigned)grid, T, 0, st>>>(a);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -10,8 +10,30 @@ namespace brm {
 
 struct RowJob;
 
-// row bins (by intermediate products nprod_i and list count L_i of a row)
-enum { kBinEmpty = 0, kBinWarp = 1, kBinBlock = 2, kBinLong = 3, kNumBins = 4 };
+// Row bins (by intermediate products nprod_i and list count L_i of a row):
+//   empty           nprod_i = 0 (the row of C is empty);
+//   register r=0..5 TPR = 2^r threads per row, nprod_i <= 32 * TPR and
+//                   L_i <= 8 * TPR, keys held in registers (brm_reg_rows.cuh);
+//   warp            one warp per row, shared-memory ping-pong (brm_rows.cuh);
+//   block           one thread block per row, shared-memory ping-pong;
+//   long            one thread block per row, device-memory ping-pong arena.
+enum {
+    kBinEmpty = 0, kBinReg0 = 1, kNumRegBins = 6, kBinWarp = kBinReg0 + kNumRegBins, kBinBlock, kBinLong, kNumBins
+};
+__host__ __device__ constexpr int reg_bin_tpr(int bin) { return 1 << (bin - kBinReg0); }
+
+// Capacities of the register bins: keys per thread, lists per thread.
+constexpr int kRegE = 32;
+constexpr int kRegListsPerThread = 8;
+constexpr int kRegMaxTpr = 32;
+constexpr int kRegMaxNprod = kRegE * kRegMaxTpr;   // 1024
+
+// Most columns B may have for a register bin with `tpr` threads per row: a
+// 32-bit key holds the column above the product's position in the row
+// (5 + log2(tpr) bits) and must stay below the all-ones padding key.
+__host__ __device__ constexpr int64_t reg_col_limit(int tpr) {
+    return (int64_t(1) << (27 - (tpr >= 32 ? 5 : tpr >= 16 ? 4 : tpr >= 8 ? 3 : tpr >= 4 ? 2 : tpr >= 2 ? 1 : 0))) - 1;
+}
 
 // Capacities of the shared-memory bins.
 constexpr int kWarpCap = 256;     // warp bin: nprod_i <= 256 and L_i <= 256
@@ -20,8 +42,8 @@ constexpr int kBlockLCap = 1024;  // ... and L_i <= 1024
 
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {
-    kPhValidate = 0, kPhBin, kPhSymWarp, kPhSymBlock, kPhSymLong, kPhScan,
-    kPhNumWarp, kPhNumBlock, kPhNumLong, kPhCompact, kNumPhases
+    kPhValidate = 0, kPhBin, kPhSymReg, kPhSymWarp, kPhSymBlock, kPhSymLong, kPhScan,
+    kPhNumReg, kPhNumWarp, kPhNumBlock, kPhNumLong, kPhCompact, kPhBackward, kNumPhases
 };
 
 // Kernel launches made by the library so far (all threads).
@@ -33,28 +55,37 @@ enum VKind { kIdx = 0, kF64 = 1, kF32 = 2, kF32C = 3 };
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st);
 size_t long_row_bytes_for(VKind v, int64_t nprod, int64_t L);
 
-// Statistics written by the binning kernel.
+// Statistics written by the binning kernels.
 struct BinStats {
     unsigned long long count[kNumBins];
     unsigned long long total_nprod;
     unsigned long long max_nprod;
     unsigned long long max_L;
     unsigned long long bad;   // validation: nonzero if an input is malformed
+    unsigned long long cursor[kNumBins];   // fill level of each bin during the scatter
 };
 
+// Binning in two passes: k_bin classifies every row (bin_of, counts); after
+// the host has read the counts, k_bin_scatter lists the rows of every bin b
+// contiguously at rows[base[b] ...] (order inside a bin is unspecified).
 struct BinArgs {
     int64_t m;
     const int32_t *arp, *acol, *brp;
+    int32_t reg_max_tpr;   // largest register-bin TPR allowed (0: none)
     int32_t warp_cap, block_cap, block_lcap;
     int64_t *nprod;        // optional, per row
-    int32_t *bin_rows[kNumBins];   // per bin row lists (bins 1..3), optional
-    int64_t *long_nprod;   // per long-bin slot: nprod_i
-    int32_t *long_L;       // per long-bin slot: L_i
+    uint8_t *bin_of;       // optional, per row: its bin
     int64_t *row_cnt;      // optional: rows of the empty bin get 0
     BinStats *st;
+    // scatter pass
+    int64_t base[kNumBins];
+    int32_t *rows;         // m entries
+    int64_t *long_nprod;   // optional, per long-bin slot: nprod_i (needs nprod)
+    int32_t *long_L;       // optional, per long-bin slot: L_i
 };
 
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t st);
+cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st);
 cudaError_t launch_validate(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rp, const int32_t *col,
                             BinStats *st, cudaStream_t stream);
 // exclusive scan of in[0..n) into out[0..n] (out[n] = total); tmp needs
@@ -64,5 +95,16 @@ cudaError_t launch_scan(const int64_t *in, int64_t *out, int64_t n, void *tmp, c
 // Upper: copy rows of C_bar (at cbar_off[i], row_size[i] long) to C at rp[i]
 cudaError_t launch_compact(int64_t m, const int64_t *cbar_off, const int64_t *rp, const int32_t *cbar_col,
                            const void *cbar_val, int32_t *col, void *val, size_t vbytes, cudaStream_t st);
+
+// Backward pass of C = A * B (brm_backward.cu).
+struct BackwardArgs {
+    int64_t m;
+    const int32_t *arp, *acol; const void *aval;
+    const int32_t *brp, *bcol; const void *bval;
+    const int64_t *crp; const int32_t *ccol; const void *dC;
+    void *dA, *dB;            // either may be null
+    unsigned int *err;        // set when C's pattern lacks a column of some B_k*
+};
+cudaError_t launch_backward(const BackwardArgs &a, bool f64, cudaStream_t st);
 
 }  // namespace brm

@@ -1,5 +1,6 @@
-// Row kernels of the three row bins, built on the BRMerge row engine.
+// Row kernels of the row bins, built on the BRMerge row engine.
 //
+//   register bins  rows of at most 1024 products: brm_reg_rows.cuh.
 //   warp bin   0 < nprod_i <= WCAP, L_i <= WCAP: one warp per row, ping-pong
 //              buffers and list offsets in the warp's slice of shared memory.
 //   block bin  nprod_i <= BCAP, L_i <= BLCAP: one thread block per row,
@@ -11,6 +12,7 @@
 
 #include "brm_engine.cuh"
 #include "brm_internal.h"
+#include "brm_reg_rows.cuh"
 
 namespace brm {
 
@@ -134,6 +136,7 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (bin >= kBinReg0 && bin < kBinReg0 + kNumRegBins) return launch_reg_rows<P>(reg_bin_tpr(bin), j, st, sms);
     if (bin == kBinWarp) {
         const size_t sm = kWarpsPerBlock * pair_bytes<P>(kWarpCap, kWarpCap);
         auto kern = k_rows_warp<P, kWarpCap>;

@@ -92,11 +92,45 @@ def test_bins_all_modes_exact(mode, dtype, comp):
 
 
 def test_bins_small_thresholds():
-    """The same rows through other bins (tiny warp / block capacities)."""
+    """The same rows through other bins: register bins limited or off, tiny
+    warp / block capacities."""
     A, B = bins_matrix(seed=4)
     ref = oracle.alg1(A, B)
-    for wcap, bcap in ((8, 64), (32, 32), (1, 2)):
-        assert_rows_exact(run(A, B, warp_max_nprod=wcap, block_max_nprod=bcap), ref)
+    for rcap, wcap, bcap in ((-1, 8, 64), (-1, 32, 32), (-1, 1, 2), (64, 0, 0), (256, 0, 0), (-1, 0, 0)):
+        assert_rows_exact(run(A, B, reg_max_nprod=rcap, warp_max_nprod=wcap, block_max_nprod=bcap), ref)
+
+
+@pytest.mark.parametrize("mode,dtype,comp", MODES)
+def test_register_bins_every_size(mode, dtype, comp):
+    """Rows of 1..1024 products and 1..256 lists (every register bin, their
+    capacity edges, duplicate-heavy and duplicate-free rows)."""
+    k, n = 3000, 2500
+    B = I.erdos_renyi(k, 4, seed=31, ncols=n)
+    Bd = I.erdos_renyi(k, 4, seed=32, ncols=40)          # few columns: long runs of duplicates
+    Ls = [1, 2, 7, 8, 9, 16, 17, 31, 32, 33, 63, 64, 65, 128, 129, 200, 255, 256]
+    for Bm in (B, Bd):
+        rows = []
+        for t, L in enumerate(Ls):
+            u = I.rand_u64(34, t, np.arange(8 * L + 64)) % np.uint64(k)
+            _, idx = np.unique(u, return_index=True)
+            rows.append(np.sort(u[np.sort(idx)][:L].astype(np.int64)))
+        arp = np.zeros(len(rows) + 1, dtype=np.int64)
+        arp[1:] = np.cumsum([len(r) for r in rows])
+        acol = np.concatenate(rows).astype(np.int32)
+        A = I.CSR(len(rows), k, arp.astype(np.int32), acol, I.rand_sym(35, 1, np.arange(len(acol))))
+        ref = oracle.alg1(A, Bm, prec=mode)
+        assert_rows_exact(run(A, Bm, "precise", dtype, comp), ref)
+        assert_rows_exact(run(A, Bm, "upper", dtype, comp), ref)
+
+
+def test_register_bins_wide_B():
+    """B with more columns than the register keys can pack for the larger
+    bins: those rows take the shared-memory kernels, the result is the same."""
+    k, n = 2000, (1 << 23) + 7
+    B = I.erdos_renyi(k, 6, seed=36, ncols=n)
+    for L, seed in ((100, 37), (40, 38), (3, 39)):   # block bin, register bins of 8 and 1 threads
+        X = I.erdos_renyi(300, L, seed=seed, ncols=k)
+        assert_rows_exact(run(X, B), oracle.alg1(X, B))
 
 
 def test_long_rows_small_arena_batches():
@@ -178,8 +212,10 @@ def test_trace_counts_launches():
     t = brm.brm_trace_read()
     brm.brm_trace_enable(was)
     assert brm.brm_kernel_launches() > n0
-    assert t["numeric_warp"][1] == 1 and t["numeric_warp"][0] > 0
-    assert t["bin"][1] == 1 and t["symbolic_warp"][1] == 1
+    # every row of the 32 x 32 Laplacian squared has <= 25 products and <= 5
+    # lists: all in the one-thread-per-row register bin
+    assert t["numeric_reg"][1] == 1 and t["numeric_reg"][0] > 0
+    assert t["bin"][1] == 2 and t["symbolic_reg"][1] == 1 and t["numeric_warp"][1] == 0
 
 
 # --------------------------------------------------------------------------
