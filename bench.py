@@ -334,6 +334,196 @@ def run_profile(args):
     print(json.dumps({"profile": "ER", "n": A.rows, "launches": brm.brm_kernel_launches()}), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the other configurations (reported beside the headline line)
+# ---------------------------------------------------------------------------
+def _timed(fn, steps, warmup):
+    """Milliseconds per call of fn (CUDA events on the current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _sample_rows(nprod, count, seed):
+    top = np.argsort(-nprod, kind="stable")[: count // 4]
+    rnd = I.rand_below(seed, 30, np.arange(count), len(nprod))
+    return np.unique(np.concatenate([top, rnd]))
+
+
+def _rows_to_host(C, rows):
+    """(row_ptr, col, val) of the given rows of a device result."""
+    import torch
+    rp = C.rp.cpu().numpy()
+    starts, ends = rp[rows], rp[rows + 1]
+    idx = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]) if len(rows) else np.zeros(0, np.int64)
+    it = torch.from_numpy(idx).to(C.col.device)
+    crp = np.zeros(len(rows) + 1, dtype=np.int64)
+    crp[1:] = np.cumsum(ends - starts)
+    return crp, C.col[it].cpu().numpy(), C.val[it].cpu().numpy().astype(np.float64)
+
+
+def run_rmat(args):
+    """R-MAT A*A: FP64 plain, FP32 plain and FP32 with TwoSum; GFLOP/s and the
+    FP32 error against the FP64 oracle on sampled rows."""
+    import torch
+    import oracle
+    from paper_2206_06611_gb300 import brm
+    torch.cuda.set_device(0)
+    A = I.rmat(args.scale, 16)
+    nprod = oracle.row_nprod(A, A)
+    total = int(nprod.sum())
+    rows = _sample_rows(nprod, 400, 17)
+    ref = oracle.gustavson(A, A, rows, with_abs=True)
+    out = {"workload": f"R-MAT scale {args.scale} ef16 dedup, C=A*A, BRMerge-Precise", "n": A.rows, "nnz_A": A.nnz,
+           "nprod": total}
+    for mode, dtype, comp in (("f64", np.float64, False), ("f32", np.float32, False), ("f32_twosum", np.float32, True)):
+        dA = brm.to_device(A, dtype=dtype)
+        C = brm.brm_spgemm_precise(dA, dA, compensated=comp)
+        torch.cuda.synchronize()
+        crp, col, val = _rows_to_host(C, rows)
+        assert np.array_equal(col, ref.col), "structure differs from the oracle"
+        d = (val - ref.val) ** 2
+        cs, ca = np.concatenate(([0.0], np.cumsum(d))), np.concatenate(([0.0], np.cumsum(ref.abs ** 2)))
+        num = np.sqrt(np.maximum(cs[crp[1:]] - cs[crp[:-1]], 0))
+        den = np.sqrt(np.maximum(ca[crp[1:]] - ca[crp[:-1]], 0))
+        err = np.where(den > 0, num / np.where(den > 0, den, 1), 0)
+        nnz_c = C.nnz
+        del C
+        torch.cuda.empty_cache()
+
+        def step():
+            Cx = brm.brm_spgemm_precise(dA, dA, compensated=comp)
+            del Cx
+
+        brm.brm_trace_reset()
+        brm.brm_trace_enable(True)
+        ms = _timed(step, args.steps, max(1, min(args.warmup, 2)))
+        t = brm.brm_trace_read()
+        brm.brm_trace_enable(False)
+        n_calls = args.steps + max(1, min(args.warmup, 2))
+        out[mode] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9, "nnz_C": nnz_c,
+                     "phases_ms": {k: round(v[0] / n_calls, 3) for k, v in t.items() if v[1]},
+                     "row_err_vs_f64_oracle": {"max": float(err.max()), "median": float(np.median(err)),
+                                               "rows": int(len(rows))}}
+        del dA
+        torch.cuda.empty_cache()
+    out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    out["speedup_f32_twosum_vs_f64"] = out["f64"]["ms_per_step"] / out["f32_twosum"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    """512 uneven products: one batched call vs 512 single calls, the numeric
+    pass replayed from a CUDA graph, autotuned bins; FP64 and FP32."""
+    import torch
+    import oracle
+    from paper_2206_06611_gb300 import brm
+    torch.cuda.set_device(0)
+    out = {"workload": "batched: 512 products A_i*A_i, n_i log-uniform in [1e3, 2e5], half 3-D Laplacian, "
+                       "half ER with 4..32 per row"}
+    mats64 = I.batched_mix(512)
+    total = int(sum(oracle.row_nprod(M, M).sum() for M in mats64))
+    for name, dtype in (("f64", np.float64), ("f32", np.float32)):
+        mats = [M.astype(dtype) for M in mats64]
+        dev = [brm.to_device(M) for M in mats]
+        gf = lambda ms: 2.0 * total / (ms * 1e-3) / 1e9  # noqa: E731
+
+        def batched():
+            C, _ = brm.brm_spgemm_batched(dev, dev)
+            del C
+
+        def separate():
+            for d in dev:
+                C = brm.brm_spgemm_precise(d, d)
+                del C
+
+        r = {"nprod": total, "rows": int(sum(M.rows for M in mats))}
+        r["separate_ms"] = _timed(separate, max(1, args.steps // 2), 1)
+        r["batched_ms"] = _timed(batched, args.steps, 2)
+        opts, tune_ms = brm.brm_autotune(dev, dev)
+        r["autotuned"] = {"reg_keys": opts["reg_keys"], "reg_warps": opts["reg_warps"], "tune_call_ms": tune_ms}
+
+        def batched_tuned():
+            C, _ = brm.brm_spgemm_batched(dev, dev, **opts)
+            del C
+
+        r["batched_tuned_ms"] = _timed(batched_tuned, args.steps, 2)
+        b = brm.Batch(dev, dev, **opts)
+        r["numeric_graph_ms"] = _timed(b.graph_launch, args.steps, 2)
+        r["numeric_launch_ms"] = _timed(b.numeric, args.steps, 2)
+        b.check()
+        b.close()
+        for k in ("separate_ms", "batched_ms", "batched_tuned_ms"):
+            r[k.replace("_ms", "_gflops")] = gf(r[k])
+        r["speedup_batched_vs_separate"] = r["separate_ms"] / r["batched_tuned_ms"]
+        out[name] = r
+        del dev
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_diff(args):
+    """Differentiable C = A*B (A R-MAT scale 18 ef16, B ER 2^18 with 8 per row,
+    FP32 N(0,1)): forward + hand-written backward, and the FP64 plain forward."""
+    import torch
+    import oracle
+    from paper_2206_06611_gb300 import brm
+    torch.cuda.set_device(0)
+    A = I.normal_values(I.rmat(18, 16), 101)
+    B = I.normal_values(I.erdos_renyi(1 << 18, 8), 102)
+    total = int(oracle.row_nprod(A, B).sum())
+    dA, dB = brm.to_device(A), brm.to_device(B)
+    a_val = dA.val.clone().requires_grad_(True)
+    b_val = dB.val.clone().requires_grad_(True)
+    Aq = brm.DeviceCSR(A.rows, A.cols, dA.rp, dA.col, a_val)
+    Bq = brm.DeviceCSR(B.rows, B.cols, dB.rp, dB.col, b_val)
+    C = brm.spgemm(Aq, Bq)
+    G = torch.from_numpy(I.rand_normal(103, I.S_GRAD, np.arange(C.nnz)).astype(np.float32)).cuda()
+    del C
+
+    def fwd():
+        Cx = brm.spgemm(Aq, Bq)
+        del Cx
+
+    def fwd_bwd():
+        Cx = brm.spgemm(Aq, Bq)
+        (Cx.val * G).sum().backward()
+        a_val.grad = None
+        b_val.grad = None
+
+    C = brm.spgemm(Aq, Bq)
+    Cd = brm.DeviceCSR(C.rows, C.cols, C.rp, C.col, None)
+    del C
+
+    def bwd_only():
+        brm.brm_spgemm_backward(dA, dB, Cd, G)
+
+    d64A, d64B = brm.to_device(A.astype(np.float64)), brm.to_device(B.astype(np.float64))
+
+    def fwd64():
+        Cx = brm.brm_spgemm_precise(d64A, d64B)
+        del Cx
+
+    out = {"workload": "differentiable C=A*B, A R-MAT scale 18 ef16, B ER 2^18 8/row, FP32 N(0,1)",
+           "nprod": total}
+    out["fwd_f32_ms"] = _timed(fwd, args.steps, 3)
+    out["bwd_f32_ms"] = _timed(bwd_only, args.steps, 3)
+    out["fwd_bwd_f32_ms"] = _timed(fwd_bwd, args.steps, 3)
+    out["fwd_f64_plain_ms"] = _timed(fwd64, args.steps, 3)
+    out["speedup_f32_fwd_vs_f64_plain"] = out["fwd_f64_plain_ms"] / out["fwd_f32_ms"]
+    out["fwd_f32_gflops"] = 2.0 * total / (out["fwd_f32_ms"] * 1e-3) / 1e9
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,9 +534,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", action="store_true", help="two calls only (for ncu captures)")
     ap.add_argument("--profile-n", type=int, default=1 << 20)
+    ap.add_argument("--workload", default="er", choices=["er", "rmat", "batched", "diff"],
+                    help="er: the headline line; the others print their own JSON line")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of --workload rmat")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.workload == "rmat":
+        run_rmat(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "diff":
+        run_diff(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

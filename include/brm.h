@@ -101,12 +101,21 @@ typedef struct {
  *                  elements in the merge tree is TwoSum-compensated (Knuth,
  *                  TAOCP vol. 2, 4.2.2): each element carries a float
  *                  running error, the stored value is sum + error.
- *   reg_max_nprod  rows with 0 < nprod <= this (at most 1024; 0 = 1024,
- *                  negative = none) and at most nprod/4 lists are merged with
- *                  their keys in registers by 1..32 threads per row, when B
- *                  has few enough columns to pack a column and a position into
- *                  32 bits (2^27 - 1 for rows of <= 32 products, halving per
- *                  doubling of the row size);
+ *   reg_max_nprod  rows with 0 < nprod <= this (at most 32 * reg_keys;
+ *                  0 = that maximum, negative = none) are merged with their
+ *                  keys in registers by 1..32 threads per row, each holding
+ *                  reg_keys products and at most reg_keys/4 lists, when B
+ *                  has few enough columns to pack a column and a position
+ *                  into 32 bits (2^32 / (threads * reg_keys) - 1);
+ *   reg_keys       8, 16 or 32 (default 16; other values give 16);
+ *   reg_warps      warps per block of the register-bin kernels, 1..8
+ *                  (default 4);
+ *   symbolic_hash  register bins count a row's distinct columns in the
+ *                  symbolic pass with the numeric pass's sorting network on
+ *                  bare columns (0, default) or by hashing into a
+ *                  shared-memory table (1, the paper's symbolic method;
+ *                  slower on GB300 because of shared-memory atomics); the
+ *                  counts are identical;
  *   warp_max_nprod other rows with 0 < nprod <= this (and <= as many lists)
  *                  are merged by one warp in shared memory (at most 256).
  *   block_max_nprod rows up to this many products are merged by one thread
@@ -122,6 +131,9 @@ typedef struct {
     int32_t warp_max_nprod;
     int32_t block_max_nprod;
     int32_t reg_max_nprod;
+    int32_t reg_keys;
+    int32_t reg_warps;
+    int32_t symbolic_hash;
     size_t arena_bytes;
 } brm_options;
 
@@ -231,6 +243,67 @@ int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t
 int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, const int32_t *C_col_idx,
                         const void *dC, void *dA_val, void *dB_val, const brm_options *opts,
                         const brm_allocator *alloc, void *stream);
+
+/*
+ * Batched products (the batching pattern added to the paper's method): count
+ * independent products C_p = A_p * B_p of uneven sizes processed as one
+ * problem -- one binning over all their rows, one launch per row bin for the
+ * symbolic pass and one for the numeric pass (BRMerge-Precise, Section
+ * III-D-2), whatever the number of products.  The result is the vertical
+ * stack of the C_p: one CSR whose rows row_offset[p] .. row_offset[p+1]-1 are
+ * the rows of C_p, with C_p's own column indices (C.cols = the largest
+ * B_p.cols).  All products must have the same dtype.
+ *   A, B        host arrays of count input descriptors (device arrays inside).
+ *   C           receives the stacked result (arrays from alloc).
+ *   row_offset  host int64[count + 1] or NULL: the first row of every C_p.
+ * Synchronises the stream as brm_spgemm_precise does, plus once to set up
+ * the product table.
+ */
+int brm_spgemm_batched(int32_t count, const brm_csr *A, const brm_csr *B, brm_csr_out *C, int64_t *row_offset,
+                       const brm_options *opts, const brm_allocator *alloc, void *stream);
+
+/*
+ * Prepared batches: brm_batch_create runs everything of brm_spgemm_batched
+ * up to the numeric pass (product table, bins, symbolic pass, allocation of
+ * C, the long-row arena) and keeps it; the numeric pass can then be run again
+ * and again on new VALUES of the same input arrays (same patterns, same
+ * pointers) -- the structure reuse of repeated products -- without any host
+ * synchronisation or allocation:
+ *   brm_batch_numeric       launches the numeric pass on stream.
+ *   brm_batch_graph_launch  the same, as a CUDA graph: the first call captures
+ *                           the launches (on a private stream) and
+ *                           instantiates the graph, every call launches it
+ *                           on stream.  The batch must not be modified while
+ *                           a graph launch is in flight.
+ *   brm_batch_check         synchronises stream and reports BRM_ERR_INVALID
+ *                           if a numeric row did not fill its symbolic slot.
+ *   brm_batch_result        the stacked C (arrays still owned by the batch).
+ *   brm_batch_take          the same, and the caller becomes the owner (free
+ *                           with brm_csr_out_free and the batch's allocator).
+ *   brm_batch_destroy       frees what the batch still owns.
+ * The allocator struct is copied; its callbacks and context must stay valid
+ * until brm_batch_destroy.  A batch is used by one host thread at a time.
+ */
+typedef struct brm_batch brm_batch;
+int brm_batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *opts,
+                     const brm_allocator *alloc, void *stream, brm_batch **out);
+int brm_batch_numeric(brm_batch *batch, void *stream);
+int brm_batch_graph_launch(brm_batch *batch, void *stream);
+int brm_batch_check(brm_batch *batch, void *stream);
+int brm_batch_result(const brm_batch *batch, brm_csr_out *C, int64_t *row_offset);
+int brm_batch_take(brm_batch *batch, brm_csr_out *C, int64_t *row_offset);
+void brm_batch_destroy(brm_batch *batch);
+
+/*
+ * Autotuner of the row bins: times brm_batch_create + brm_batch_numeric for
+ * every candidate shape of the register bins (reg_keys 8, 16, 32 x reg_warps
+ * 2, 4, 8; the other fields are taken from base) on the given products and
+ * writes the fastest options to best (and its time in milliseconds to
+ * best_ms, if not NULL).  Each candidate runs once to warm up and twice
+ * timed (the minimum counts).  Synchronises the stream many times.
+ */
+int brm_autotune(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *base, brm_options *best,
+                 double *best_ms, const brm_allocator *alloc, void *stream);
 
 /* Frees the arrays of a brm_csr_out with the given allocator and zeroes it. */
 void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);

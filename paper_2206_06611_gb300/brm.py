@@ -51,7 +51,8 @@ class brm_allocator(ctypes.Structure):
 class brm_options(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("compensated", ctypes.c_int32),
                 ("warp_max_nprod", ctypes.c_int32), ("block_max_nprod", ctypes.c_int32),
-                ("reg_max_nprod", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t)]
+                ("reg_max_nprod", ctypes.c_int32), ("reg_keys", ctypes.c_int32), ("reg_warps", ctypes.c_int32),
+                ("symbolic_hash", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t)]
 
 
 class BrmError(RuntimeError):
@@ -97,6 +98,20 @@ def load(build_if_needed: bool = True):
     lib.brm_spgemm_numeric_noalloc.argtypes = [pcsr, pcsr, P, P, P, popt, P]
     lib.brm_spgemm_backward.argtypes = [pcsr, pcsr, P, P, P, P, P, popt, pal, P]
     lib.brm_spgemm_backward.restype = ctypes.c_int
+    I32 = ctypes.c_int32
+    lib.brm_spgemm_batched.argtypes = [I32, pcsr, pcsr, pout, P, popt, pal, P]
+    lib.brm_batch_create.argtypes = [I32, pcsr, pcsr, popt, pal, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.brm_batch_numeric.argtypes = [P, P]
+    lib.brm_batch_graph_launch.argtypes = [P, P]
+    lib.brm_batch_check.argtypes = [P, P]
+    lib.brm_batch_result.argtypes = [P, pout, P]
+    lib.brm_batch_take.argtypes = [P, pout, P]
+    lib.brm_batch_destroy.argtypes = [P]
+    lib.brm_batch_destroy.restype = None
+    lib.brm_autotune.argtypes = [I32, pcsr, pcsr, popt, popt, ctypes.POINTER(ctypes.c_double), pal, P]
+    for f in (lib.brm_spgemm_batched, lib.brm_batch_create, lib.brm_batch_numeric, lib.brm_batch_graph_launch,
+              lib.brm_batch_check, lib.brm_batch_result, lib.brm_batch_take, lib.brm_autotune):
+        f.restype = ctypes.c_int
     for f in (lib.brm_spgemm_symbolic, lib.brm_spgemm_precise, lib.brm_spgemm_upper, lib.brm_row_nprod,
               lib.brm_spgemm_numeric_noalloc):
         f.restype = ctypes.c_int
@@ -227,7 +242,7 @@ def _stream(stream=None):
 
 
 def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
-            arena_bytes=0) -> brm_options:
+            reg_keys=0, reg_warps=0, symbolic_hash=False, arena_bytes=0) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -238,6 +253,11 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
         o.block_max_nprod = block_max_nprod
     if reg_max_nprod:
         o.reg_max_nprod = reg_max_nprod
+    if reg_keys:
+        o.reg_keys = reg_keys
+    if reg_warps:
+        o.reg_warps = reg_warps
+    o.symbolic_hash = int(bool(symbolic_hash))
     o.arena_bytes = arena_bytes
     return o
 
@@ -328,6 +348,118 @@ def brm_spgemm_backward(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, dC, want_da=Tr
                                    ctypes.c_void_p(dB.data_ptr() if dB is not None and B.nnz else None),
                                    None, ctypes.byref(_allocator().struct), _stream(stream)))
     return dA, dB
+
+
+# ---------------------------------------------------------------------------
+# batched products
+# ---------------------------------------------------------------------------
+def _csr_array(Ms):
+    arr = (brm_csr * max(len(Ms), 1))()
+    for i, M in enumerate(Ms):
+        arr[i] = _csr_struct(M)
+    return arr
+
+
+def _options_from(o: brm_options) -> dict:
+    return {f: getattr(o, f) for f, _ in brm_options._fields_}
+
+
+def _stacked(al, C: brm_csr_out, dtype, take: bool) -> DeviceCSR:
+    import torch
+    if take:
+        return _result(al, C, dtype)
+    rp = al.live[C.row_ptr].view(torch.int64)[:C.rows + 1]
+    col = al.live[C.col_idx].view(torch.int32)[:C.nnz]
+    val = al.live[C.val].view(dtype)[:C.nnz]
+    return DeviceCSR(C.rows, C.cols, rp, col, val)
+
+
+def brm_spgemm_batched(As, Bs, *, stream=None, **opts):
+    """C_p = A_p * B_p for all p in one batched BRMerge-Precise call.
+    Returns (the stacked C as a DeviceCSR, row offsets: a list of count + 1)."""
+    if len(As) != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    lib = load()
+    a, b = _csr_array(As), _csr_array(Bs)
+    o = options(**opts)
+    al = _allocator()
+    C = brm_csr_out()
+    off = (ctypes.c_int64 * (len(As) + 1))()
+    _check(lib.brm_spgemm_batched(len(As), a, b, ctypes.byref(C), ctypes.cast(off, ctypes.c_void_p), ctypes.byref(o),
+                                  ctypes.byref(al.struct), _stream(stream)))
+    return _result(al, C, As[0].val.dtype), list(off)
+
+
+def split(C: DeviceCSR, offsets, cols=None):
+    """The products of a stacked result as DeviceCSRs (views of C's arrays;
+    each row pointer rebased to start at 0)."""
+    out = []
+    for p in range(len(offsets) - 1):
+        r0, r1 = offsets[p], offsets[p + 1]
+        rp = C.rp[r0:r1 + 1]
+        base = int(rp[0].item()) if r1 >= r0 else 0
+        lo, hi = base, int(rp[-1].item())
+        out.append(DeviceCSR(r1 - r0, C.cols if cols is None else cols[p], rp - base, C.col[lo:hi], C.val[lo:hi]))
+    return out
+
+
+class Batch:
+    """A prepared batch (brm_batch_*): symbolic pass done and C allocated;
+    numeric() / graph_launch() recompute C's values from the current values
+    of the same input arrays."""
+
+    def __init__(self, As, Bs, *, stream=None, **opts):
+        if len(As) != len(Bs):
+            raise ValueError("As and Bs differ in length")
+        self.lib = load()
+        self.As, self.Bs = list(As), list(Bs)          # keep the inputs alive
+        a, b = _csr_array(self.As), _csr_array(self.Bs)
+        o = options(**opts)
+        self.al = _allocator()
+        h = ctypes.c_void_p()
+        _check(self.lib.brm_batch_create(len(As), a, b, ctypes.byref(o), ctypes.byref(self.al.struct),
+                                         _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.dtype = As[0].val.dtype if As else None
+
+    def numeric(self, stream=None):
+        _check(self.lib.brm_batch_numeric(self.h, _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(self.lib.brm_batch_graph_launch(self.h, _stream(stream)))
+
+    def check(self, stream=None):
+        _check(self.lib.brm_batch_check(self.h, _stream(stream)))
+
+    def result(self):
+        """(stacked C as views of the batch's arrays, row offsets)."""
+        C = brm_csr_out()
+        off = (ctypes.c_int64 * (len(self.As) + 1))()
+        _check(self.lib.brm_batch_result(self.h, ctypes.byref(C), ctypes.cast(off, ctypes.c_void_p)))
+        return _stacked(self.al, C, self.dtype, take=False), list(off)
+
+    def close(self):
+        if self.h:
+            self.lib.brm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def brm_autotune(As, Bs, *, stream=None, **base):
+    """(the fastest options as a dict, its milliseconds) for these products."""
+    lib = load()
+    a, b = _csr_array(As), _csr_array(Bs)
+    o = options(**base)
+    best = brm_options()
+    ms = ctypes.c_double(0)
+    _check(lib.brm_autotune(len(As), a, b, ctypes.byref(o), ctypes.byref(best), ctypes.byref(ms),
+                            ctypes.byref(_allocator().struct), _stream(stream)))
+    return _options_from(best), float(ms.value)
 
 
 def _spgemm_fn():

@@ -2,6 +2,7 @@
 // pipelines (Section III-D), workspace through the caller's allocator, and the
 // extern "C" entry points declared in include/brm.h.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -75,7 +76,7 @@ struct PhaseScope {
     cudaEvent_t a = nullptr;
     long long n0;
     PhaseScope(int phase, cudaStream_t s) : ph(phase), st(s), n0(g_launches.load()) {
-        if (g_trace.on) {
+        if (g_trace.on && phase >= 0) {
             std::lock_guard<std::mutex> lk(g_trace.mu);
             a = g_trace.event();
             if (a) cudaEventRecord(a, st);
@@ -169,6 +170,32 @@ int check_pair(const brm_csr *A, const brm_csr *B, bool need_val) {
     return BRM_OK;
 }
 
+// The inputs of one pass: one product A * B, or a batch of products whose
+// rows are stacked (row r of the stack is row r - row0[p] of product p).
+struct Src {
+    int64_t m = 0;           // rows of C (stacked rows for a batch)
+    int64_t bcols = 0;       // columns of B (the largest over a batch)
+    int32_t dtype = BRM_F64;
+    const int32_t *arp = nullptr, *acol = nullptr, *brp = nullptr, *bcol = nullptr;
+    const void *aval = nullptr, *bval = nullptr;
+    const ProdDesc *prods = nullptr;   // batch: device table of the products
+    const int32_t *prod_of = nullptr;  // batch: product of every stacked row
+};
+
+Src src_of(const brm_csr *A, const brm_csr *B) {
+    Src s;
+    s.m = A->rows;
+    s.bcols = B->cols;
+    s.dtype = A->dtype;
+    s.arp = A->row_ptr;
+    s.acol = A->col_idx;
+    s.aval = A->val;
+    s.brp = B->row_ptr;
+    s.bcol = B->col_idx;
+    s.bval = B->val;
+    return s;
+}
+
 brm_options resolve(const brm_options *o) {
     brm_options r;
     brm_options_default(&r);
@@ -176,17 +203,19 @@ brm_options resolve(const brm_options *o) {
     if (r.warp_max_nprod <= 0 || r.warp_max_nprod > kWarpCap) r.warp_max_nprod = kWarpCap;
     if (r.block_max_nprod <= 0 || r.block_max_nprod > kBlockCap) r.block_max_nprod = kBlockCap;
     if (r.block_max_nprod < r.warp_max_nprod) r.block_max_nprod = r.warp_max_nprod;
-    if (r.reg_max_nprod == 0 || r.reg_max_nprod > kRegMaxNprod) r.reg_max_nprod = kRegMaxNprod;
+    if (r.reg_keys != 8 && r.reg_keys != 16 && r.reg_keys != 32) r.reg_keys = kRegKeysDefault;
+    if (r.reg_warps < 1 || r.reg_warps > 8) r.reg_warps = kRegWarpsDefault;
+    if (r.reg_max_nprod == 0 || r.reg_max_nprod > r.reg_keys * kRegMaxTpr) r.reg_max_nprod = r.reg_keys * kRegMaxTpr;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
 
 // Largest threads-per-row of a register bin usable for this product: its
 // capacity within reg_max_nprod and B's column count packable into its keys.
-int reg_max_tpr(const brm_options &o, const brm_csr *B) {
+int reg_max_tpr(const brm_options &o, int64_t bcols) {
     int best = 0;
     for (int tpr = 1; tpr <= kRegMaxTpr; tpr <<= 1)
-        if (kRegE * tpr <= o.reg_max_nprod && B->cols <= reg_col_limit(tpr)) best = tpr;
+        if (o.reg_keys * tpr <= o.reg_max_nprod && bcols <= reg_col_limit(tpr, o.reg_keys)) best = tpr;
     return best;
 }
 
@@ -223,9 +252,8 @@ int validate_inputs(Mem &mem, const brm_csr *A, const brm_csr *B) {
 }
 
 // Step 1 (+ the GPU form of step 2): product counts, bins, long-row order.
-int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o, Plan &pl, int64_t *nprod,
-              int64_t *row_cnt) {
-    const int64_t m = A->rows;
+int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *nprod, int64_t *row_cnt) {
+    const int64_t m = src.m;
     const size_t m1 = (size_t)std::max<int64_t>(m, 1);
     BinStats *st;
     int rc = get(mem, st, 1, "bin statistics");
@@ -237,10 +265,13 @@ int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o
     if (!nprod && (rc = get(mem, nprod, m1, "row nprod"))) return rc;
     BinArgs a{};
     a.m = m;
-    a.arp = A->row_ptr;
-    a.acol = A->col_idx;
-    a.brp = B->row_ptr;
-    a.reg_max_tpr = reg_max_tpr(o, B);
+    a.arp = src.arp;
+    a.acol = src.acol;
+    a.brp = src.brp;
+    a.prods = src.prods;
+    a.prod_of = src.prod_of;
+    a.reg_max_tpr = reg_max_tpr(o, src.bcols);
+    a.reg_keys = o.reg_keys;
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;
@@ -305,20 +336,18 @@ int make_plan(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o
     return BRM_OK;
 }
 
-// One BRMerge pass (symbolic or numeric) over all bins.
-int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
-    for (int b = kBinReg0; b <= kBinBlock; ++b) {
-        RowJob jb = j;
-        jb.rows = pl.rows + pl.base[b];
-        jb.count = (int32_t)pl.stats.count[b];
-        if (jb.count == 0) continue;
-        const int ph = b < kBinWarp ? kPhSymReg : kPhSymWarp + (b - kBinWarp);
-        PhaseScope ps(v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg), mem.st);
-        BRM_CUDA(launch_rows(v, b, jb, mem.st));
-    }
+// Device-memory arena of the long rows of one pass: the long slots (longest
+// first) cut into batches whose ping-pong slices fit the budget.
+struct LongPlan {
+    std::vector<int64_t> starts;    // batch boundaries over the long slots
+    int64_t *off_d = nullptr;       // device: arena offset of every long slot
+    char *arena = nullptr;
+};
+
+int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, LongPlan &lp) {
     const int64_t nl = (int64_t)pl.long_rows_h.size();
+    lp.starts.clear();
     if (nl == 0) return BRM_OK;
-    // batches of long rows whose arena slices fit the budget
     std::vector<int64_t> need(nl);
     size_t biggest = 0;
     for (int64_t s = 0; s < nl; ++s) {
@@ -333,37 +362,61 @@ int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) 
     }
     budget = std::max(budget, biggest);
     std::vector<int64_t> off(nl);
-    std::vector<int64_t> starts;
     size_t cur = 0, maxbatch = 0;
     for (int64_t s = 0; s < nl; ++s) {
         if (s == 0 || cur + (size_t)need[s] > budget) {
-            starts.push_back(s);
+            lp.starts.push_back(s);
             cur = 0;
         }
         off[s] = (int64_t)cur;
         cur += (size_t)need[s];
         maxbatch = std::max(maxbatch, cur);
     }
-    starts.push_back(nl);
-    int64_t *off_d;
-    int rc = get(mem, off_d, nl, "arena offsets");
+    lp.starts.push_back(nl);
+    int rc = get(mem, lp.off_d, nl, "arena offsets");
     if (rc) return rc;
-    char *arena;
-    if ((rc = get(mem, arena, maxbatch, "long-row arena"))) return rc;
-    BRM_CUDA(cudaMemcpyAsync(off_d, off.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
-    PhaseScope ps(v == kIdx ? kPhSymLong : kPhNumLong, mem.st);
-    for (size_t bi = 0; bi + 1 < starts.size(); ++bi) {
-        RowJob jb = j;
-        jb.rows = pl.long_rows_s + starts[bi];
-        jb.count = (int32_t)(starts[bi + 1] - starts[bi]);
-        jb.arena = arena;
-        jb.arena_off = off_d + starts[bi];
-        jb.slot_nprod = pl.long_nprod_s + starts[bi];
-        BRM_CUDA(launch_rows(v, kBinLong, jb, mem.st));
-    }
+    if ((rc = get(mem, lp.arena, maxbatch, "long-row arena"))) return rc;
+    BRM_CUDA(cudaMemcpyAsync(lp.off_d, off.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
-    mem.free_one(arena);
-    mem.free_one(off_d);
+    return BRM_OK;
+}
+
+// Kernel launches of one pass over every bin (no host synchronisation, no
+// allocation: a numeric pass of a prepared plan can be captured in a graph).
+int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cudaStream_t st, bool trace) {
+    for (int b = kBinReg0; b <= kBinBlock; ++b) {
+        RowJob jb = j;
+        jb.rows = pl.rows + pl.base[b];
+        jb.count = (int32_t)pl.stats.count[b];
+        if (jb.count == 0) continue;
+        const int ph = b < kBinWarp ? kPhSymReg : kPhSymWarp + (b - kBinWarp);
+        PhaseScope ps(trace ? (v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg)) : -1, st);
+        BRM_CUDA(launch_rows(v, b, jb, st));
+    }
+    if (lp.starts.size() < 2) return BRM_OK;
+    PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
+    for (size_t bi = 0; bi + 1 < lp.starts.size(); ++bi) {
+        RowJob jb = j;
+        jb.rows = pl.long_rows_s + lp.starts[bi];
+        jb.count = (int32_t)(lp.starts[bi + 1] - lp.starts[bi]);
+        jb.arena = lp.arena;
+        jb.arena_off = lp.off_d + lp.starts[bi];
+        jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
+        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
+    }
+    return BRM_OK;
+}
+
+// One BRMerge pass (symbolic or numeric) over all bins.
+int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
+    LongPlan lp;
+    int rc = plan_long(mem, v, pl, o, lp);
+    if (rc) return rc;
+    if ((rc = launch_pass(v, pl, lp, j, mem.st, true))) return rc;
+    if (lp.arena) {
+        mem.free_one(lp.arena);   // stream-ordered release after the launches
+        mem.free_one(lp.off_d);
+    }
     return BRM_OK;
 }
 
@@ -376,33 +429,37 @@ int check_flag(Mem &mem, const unsigned int *err) {
     return BRM_OK;
 }
 
-RowJob base_job(const brm_csr *A, const brm_csr *B) {
+RowJob base_job(const Src &src, const brm_options &o) {
     RowJob j{};
-    j.arp = A->row_ptr;
-    j.acol = A->col_idx;
-    j.aval = A->val;
-    j.brp = B->row_ptr;
-    j.bcol = B->col_idx;
-    j.bval = B->val;
+    j.prods = src.prods;
+    j.prod_of = src.prod_of;
+    j.reg_keys = o.reg_keys;
+    j.reg_warps = o.reg_warps;
+    j.sym_hash = o.symbolic_hash ? 1 : 0;
+    j.arp = src.arp;
+    j.acol = src.acol;
+    j.aval = src.aval;
+    j.brp = src.brp;
+    j.bcol = src.bcol;
+    j.bval = src.bval;
     return j;
 }
 
-VKind value_kind(const brm_csr *A, const brm_options &o) {
-    if (A->dtype == BRM_F64) return kF64;
+VKind value_kind(int32_t dtype, const brm_options &o) {
+    if (dtype == BRM_F64) return kF64;
     return o.compensated ? kF32C : kF32;
 }
 
 size_t value_bytes(int32_t dtype) { return dtype == BRM_F64 ? 8 : 4; }
 
 // Symbolic phase into row_ptr (m+1, device); returns nnz(C) on the host.
-int symbolic_into(Mem &mem, const brm_csr *A, const brm_csr *B, const brm_options &o, Plan &pl, int64_t *row_ptr,
-                  int64_t *nnz) {
-    const int64_t m = A->rows;
+int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *row_ptr, int64_t *nnz) {
+    const int64_t m = src.m;
     int64_t *row_nnz;
     int rc = get(mem, row_nnz, (size_t)std::max<int64_t>(m, 1), "row counts");
     if (rc) return rc;
-    if ((rc = make_plan(mem, A, B, o, pl, nullptr, row_nnz))) return rc;
-    RowJob j = base_job(A, B);
+    if ((rc = make_plan(mem, src, o, pl, nullptr, row_nnz))) return rc;
+    RowJob j = base_job(src, o);
     j.out_cnt = row_nnz;
     if ((rc = run_pass(mem, kIdx, pl, o, j))) return rc;
     void *tmp;
@@ -432,12 +489,13 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
     Plan pl;
     int64_t nnz = 0;
-    if ((rc = symbolic_into(mem, A, B, o, pl, rp, &nnz))) return rc;
+    const Src src = src_of(A, B);
+    if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz))) return rc;
     int32_t *col;
     if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
     void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
     if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
-    RowJob j = base_job(A, B);
+    RowJob j = base_job(src, o);
     j.out_rp = rp;
     j.out_col = col;
     j.out_val = val;
@@ -446,7 +504,7 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
     j.exact = 1;
-    if ((rc = run_pass(mem, value_kind(A, o), pl, o, j))) return rc;
+    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
     if ((rc = check_flag(mem, err))) return rc;
     mem.detach(rp);
     mem.detach(col);
@@ -477,7 +535,8 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     if ((rc = get(mem, row_size, (size_t)std::max<int64_t>(m, 1), "row sizes"))) return rc;
     if ((rc = get(mem, cbar_off, (size_t)m + 1, "C_bar offsets"))) return rc;
     Plan pl;
-    if ((rc = make_plan(mem, A, B, o, pl, nprod, row_size))) return rc;
+    const Src src = src_of(A, B);
+    if ((rc = make_plan(mem, src, o, pl, nprod, row_size))) return rc;
     void *tmp;
     if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
     // steps 1 and 3: prefix sum of the upper bounds, temporary C_bar
@@ -491,7 +550,7 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     void *cval = mem.get((size_t)std::max<int64_t>(total, 1) * vb);
     if (!cval) return fail(BRM_ERR_OOM, "allocation of C_bar values (%lld products) failed", (long long)total);
     // step 4: BRMerge into C_bar, recording the row sizes
-    RowJob j = base_job(A, B);
+    RowJob j = base_job(src, o);
     j.out_rp = cbar_off;
     j.out_col = ccol;
     j.out_val = cval;
@@ -500,7 +559,7 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
-    if ((rc = run_pass(mem, value_kind(A, o), pl, o, j))) return rc;
+    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
     // step 5: prefix sum of the row sizes, allocation of C
     if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
     {
@@ -533,6 +592,197 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     return BRM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched products: C_p = A_p * B_p for p = 0 .. count-1, processed as one
+// stacked problem.  Row r of the stack is row r - row0[p] of product p; the
+// kernels find each row's A and B through a device table of the products, so
+// every bin of every product is served by one launch per bin, and the result
+// is the vertical stack of the C_p (one int64 row pointer, columns in each
+// product's own column space).
+// ---------------------------------------------------------------------------
+int batch_setup(Mem &mem, int32_t count, const brm_csr *A, const brm_csr *B, const brm_options &o, Src &src,
+                std::vector<int64_t> &row0) {
+    if (count < 0) return fail(BRM_ERR_INVALID, "count is negative");
+    if (count > 0 && (!A || !B)) return fail(BRM_ERR_INVALID, "A and B must not be NULL");
+    std::vector<ProdDesc> d((size_t)std::max(count, 1));
+    std::vector<int64_t> rows_of((size_t)std::max(count, 1), 0);
+    row0.assign((size_t)count + 1, 0);
+    int64_t M = 0, bcols = 0;
+    const int32_t dtype = count > 0 ? A[0].dtype : BRM_F64;
+    for (int32_t p = 0; p < count; ++p) {
+        int rc = check_pair(&A[p], &B[p], true);
+        if (rc) return fail(rc, "product %d: %s", p, g_err.c_str());
+        if (A[p].dtype != dtype) return fail(BRM_ERR_DTYPE, "product %d has another dtype than product 0", p);
+        d[p] = ProdDesc{A[p].row_ptr, A[p].col_idx, A[p].val, B[p].row_ptr, B[p].col_idx, B[p].val, M};
+        row0[p] = M;
+        rows_of[p] = A[p].rows;
+        M += A[p].rows;
+        bcols = std::max<int64_t>(bcols, B[p].cols);
+    }
+    row0[count] = M;
+    if (M >= INT32_MAX) return fail(BRM_ERR_OVERFLOW, "the batch has %lld rows (limit 2^31-1)", (long long)M);
+    if (o.validate)
+        for (int32_t p = 0; p < count; ++p) {
+            int rc = validate_inputs(mem, &A[p], &B[p]);
+            if (rc) return fail(rc, "product %d: %s", p, g_err.c_str());
+        }
+    ProdDesc *dd;
+    int64_t *ro;
+    int32_t *po;
+    int rc = get(mem, dd, d.size(), "product table");
+    if (rc) return rc;
+    if ((rc = get(mem, ro, rows_of.size(), "product rows"))) return rc;
+    if ((rc = get(mem, po, (size_t)std::max<int64_t>(M, 1), "row products"))) return rc;
+    BRM_CUDA(cudaMemcpyAsync(dd, d.data(), d.size() * sizeof(ProdDesc), cudaMemcpyHostToDevice, mem.st));
+    BRM_CUDA(cudaMemcpyAsync(ro, rows_of.data(), rows_of.size() * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
+    BRM_CUDA(launch_fill_prod_of(dd, ro, count, po, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host tables must outlive the copies
+    src = Src{};
+    src.m = M;
+    src.bcols = bcols;
+    src.dtype = dtype;
+    src.prods = dd;
+    src.prod_of = po;
+    return BRM_OK;
+}
+
+}  // namespace
+}  // namespace brm
+
+// A prepared batch (opaque in brm.h): the symbolic pass is done, C is
+// allocated and the long-row arena is planned, so the numeric pass is kernel
+// launches only and can be replayed (on new values of the same patterns) or
+// captured in a CUDA graph.
+struct brm_batch {
+    brm_allocator al{};
+    bool has_al = false;
+    brm::Mem mem;
+    brm_options o{};
+    brm::Src src;
+    brm::Plan pl;
+    brm::LongPlan lp;
+    brm::RowJob job{};
+    brm::VKind v = brm::kF64;
+    int32_t count = 0;
+    int64_t nnz = 0;
+    std::vector<int64_t> row0;
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    void *val = nullptr;
+    unsigned int *err = nullptr;
+    bool taken = false;
+    cudaStream_t cap = nullptr;          // private stream for graph capture
+    cudaGraphExec_t exec = nullptr;
+    long long graph_launches = 0;        // kernels in the captured graph
+
+    brm_batch(const brm_allocator *a, cudaStream_t s)
+        : al(a ? *a : brm_allocator{}), has_al(a != nullptr), mem(has_al ? &al : nullptr, s) {}
+    ~brm_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+        if (taken) {
+            mem.detach(rp);
+            mem.detach(col);
+            mem.detach(val);
+        }
+    }
+};
+
+namespace brm {
+namespace {
+
+int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *opts,
+                 const brm_allocator *al, cudaStream_t st, brm_batch **out) {
+    if (!out) return fail(BRM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    brm_batch *b = new brm_batch(al, st);
+    b->o = resolve(opts);
+    b->count = count;
+    int rc = batch_setup(b->mem, count, A, B, b->o, b->src, b->row0);
+    const int64_t M = b->src.m;
+    if (!rc) rc = get(b->mem, b->rp, (size_t)M + 1, "C.row_ptr");
+    if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz);
+    if (!rc) rc = get(b->mem, b->col, (size_t)std::max<int64_t>(b->nnz, 1), "C.col_idx");
+    if (!rc) {
+        b->val = b->mem.get((size_t)std::max<int64_t>(b->nnz, 1) * value_bytes(b->src.dtype));
+        if (!b->val) rc = fail(BRM_ERR_OOM, "allocation of C.val failed");
+    }
+    if (!rc) rc = get(b->mem, b->err, 1, "error flag");
+    b->v = value_kind(b->src.dtype, b->o);
+    if (!rc) rc = plan_long(b->mem, b->v, b->pl, b->o, b->lp);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    RowJob j = base_job(b->src, b->o);
+    j.out_rp = b->rp;
+    j.out_col = b->col;
+    j.out_val = b->val;
+    j.err = b->err;
+    j.exact = 1;
+    b->job = j;
+    *out = b;
+    return BRM_OK;
+}
+
+// The numeric pass of a prepared batch: launches only.
+int batch_numeric(brm_batch *b, cudaStream_t st, bool trace) {
+    BRM_CUDA(cudaMemsetAsync(b->err, 0, sizeof(unsigned int), st));
+    return launch_pass(b->v, b->pl, b->lp, b->job, st, trace);
+}
+
+int batch_check(brm_batch *b, cudaStream_t st) {
+    unsigned int h = 0;
+    BRM_CUDA(cudaMemcpyAsync(&h, b->err, sizeof h, cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(BRM_ERR_INVALID, "a numeric row length disagrees with its symbolic count");
+    return BRM_OK;
+}
+
+int batch_graph_launch(brm_batch *b, cudaStream_t st) {
+    if (!b->exec) {
+        if (!b->cap) BRM_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        // the batch's memory was made on the creation stream: order the
+        // capture stream after it once
+        BRM_CUDA(cudaStreamSynchronize(b->mem.st));
+        const long long n0 = g_launches.load();
+        BRM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+        const int rc = batch_numeric(b, b->cap, false);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        b->graph_launches = g_launches.load() - n0;
+        g_launches.fetch_sub(b->graph_launches);   // counted when the graph runs
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BRM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+            b->exec = nullptr;
+            return fail(BRM_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e2));
+        }
+    }
+    BRM_CUDA(cudaGraphLaunch(b->exec, st));
+    g_launches.fetch_add(b->graph_launches);
+    return BRM_OK;
+}
+
+void batch_result(const brm_batch *b, brm_csr_out *C, int64_t *row_offset) {
+    if (C) {
+        C->rows = b->src.m;
+        C->cols = b->src.bcols;
+        C->nnz = b->nnz;
+        C->row_ptr = b->rp;
+        C->col_idx = b->col;
+        C->val = b->val;
+        C->dtype = b->src.dtype;
+    }
+    if (row_offset)
+        for (size_t p = 0; p < b->row0.size(); ++p) row_offset[p] = b->row0[p];
+}
+
 }  // namespace
 }  // namespace brm
 
@@ -548,6 +798,9 @@ void brm_options_default(brm_options *o) {
     o->warp_max_nprod = kWarpCap;
     o->block_max_nprod = kBlockCap;
     o->reg_max_nprod = kRegMaxNprod;
+    o->reg_keys = kRegKeysDefault;
+    o->reg_warps = kRegWarpsDefault;
+    o->symbolic_hash = 0;
     o->arena_bytes = 0;
 }
 
@@ -581,7 +834,7 @@ int brm_spgemm_symbolic(const brm_csr *A, const brm_csr *B, int64_t *C_row_ptr, 
     Mem mem(alloc, static_cast<cudaStream_t>(stream));
     if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
     Plan pl;
-    rc = symbolic_into(mem, A, B, o, pl, C_row_ptr, nnz_C);
+    rc = symbolic_into(mem, src_of(A, B), o, pl, C_row_ptr, nnz_C);
     g_trace.flush();
     return rc;
 }
@@ -654,6 +907,7 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
     a.acol = A->col_idx;
     a.brp = B->row_ptr;
     a.reg_max_tpr = 0;
+    a.reg_keys = kRegKeysDefault;
     a.warp_cap = kWarpCap;
     a.block_cap = kBlockCap;
     a.block_lcap = kBlockLCap;
@@ -705,6 +959,114 @@ int brm_trace_read(double *ms, int64_t *launches, int n) {
 const char *brm_trace_phase_name(int i) { return (i >= 0 && i < kNumPhases) ? kPhaseNames[i] : ""; }
 
 int64_t brm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"
+
+extern "C" {
+
+int brm_batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *opts,
+                     const brm_allocator *alloc, void *stream, brm_batch **out) {
+    g_err.clear();
+    const int rc = batch_create(count, A, B, opts, alloc, static_cast<cudaStream_t>(stream), out);
+    g_trace.flush();
+    return rc;
+}
+
+int brm_batch_numeric(brm_batch *b, void *stream) {
+    g_err.clear();
+    if (!b) return fail(BRM_ERR_INVALID, "batch is NULL");
+    const int rc = batch_numeric(b, static_cast<cudaStream_t>(stream), true);
+    g_trace.flush();
+    return rc;
+}
+
+int brm_batch_graph_launch(brm_batch *b, void *stream) {
+    g_err.clear();
+    if (!b) return fail(BRM_ERR_INVALID, "batch is NULL");
+    return batch_graph_launch(b, static_cast<cudaStream_t>(stream));
+}
+
+int brm_batch_check(brm_batch *b, void *stream) {
+    g_err.clear();
+    if (!b) return fail(BRM_ERR_INVALID, "batch is NULL");
+    return batch_check(b, static_cast<cudaStream_t>(stream));
+}
+
+int brm_batch_result(const brm_batch *b, brm_csr_out *C, int64_t *row_offset) {
+    g_err.clear();
+    if (!b) return fail(BRM_ERR_INVALID, "batch is NULL");
+    batch_result(b, C, row_offset);
+    return BRM_OK;
+}
+
+int brm_batch_take(brm_batch *b, brm_csr_out *C, int64_t *row_offset) {
+    g_err.clear();
+    if (!b) return fail(BRM_ERR_INVALID, "batch is NULL");
+    if (b->taken) return fail(BRM_ERR_INVALID, "the result was already taken");
+    batch_result(b, C, row_offset);
+    b->taken = true;
+    return BRM_OK;
+}
+
+void brm_batch_destroy(brm_batch *b) { delete b; }
+
+int brm_autotune(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *base, brm_options *best,
+                 double *best_ms, const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    if (!best) return fail(BRM_ERR_INVALID, "best is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const brm_options b0 = resolve(base);
+    double top = 1e300;
+    brm_options win = b0;
+    static const int kKeys[] = {8, 16, 32};
+    static const int kWarps[] = {2, 4, 8};
+    for (int keys : kKeys)
+        for (int warps : kWarps) {
+            brm_options o = b0;
+            o.reg_keys = keys;
+            o.reg_warps = warps;
+            o.reg_max_nprod = 0;   // the full register range of this shape
+            double ms = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                BRM_CUDA(cudaStreamSynchronize(st));
+                const auto t0 = std::chrono::steady_clock::now();
+                brm_batch *b = nullptr;
+                int rc = batch_create(count, A, B, &o, alloc, st, &b);
+                if (!rc) rc = batch_numeric(b, st, false);
+                if (!rc) rc = batch_check(b, st);
+                const auto t1 = std::chrono::steady_clock::now();
+                delete b;
+                if (rc) return rc;
+                if (rep > 0) ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            if (ms < top) {
+                top = ms;
+                win = resolve(&o);
+            }
+        }
+    *best = win;
+    if (best_ms) *best_ms = top;
+    return BRM_OK;
+}
+
+int brm_spgemm_batched(int32_t count, const brm_csr *A, const brm_csr *B, brm_csr_out *C, int64_t *row_offset,
+                       const brm_options *opts, const brm_allocator *alloc, void *stream) {
+    g_err.clear();
+    if (!C) return fail(BRM_ERR_INVALID, "C is NULL");
+    std::memset(C, 0, sizeof *C);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    brm_batch *b = nullptr;
+    int rc = batch_create(count, A, B, opts, alloc, st, &b);
+    if (!rc) rc = batch_numeric(b, st, true);
+    if (!rc) rc = batch_check(b, st);
+    if (!rc) {
+        batch_result(b, C, row_offset);
+        b->taken = true;
+    }
+    delete b;
+    g_trace.flush();
+    return rc;
+}
 
 }  // extern "C"
 
@@ -785,7 +1147,8 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.brp = B->row_ptr;
-    a.reg_max_tpr = reg_max_tpr(o, B);
+    a.reg_max_tpr = reg_max_tpr(o, B->cols);
+    a.reg_keys = o.reg_keys;
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;
@@ -806,13 +1169,13 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
         if (b != kBinEmpty) off += (int64_t)h.count[b];
     }
     BRM_CUDA(launch_bin_scatter(a, st));
-    RowJob j = base_job(A, B);
+    RowJob j = base_job(src_of(A, B), o);
     j.out_rp = C_row_ptr;
     j.out_col = C_col;
     j.out_val = C_val;
     j.err = err;
     j.exact = 1;
-    const VKind v = value_kind(A, o);
+    const VKind v = value_kind(A->dtype, o);
     for (int b = kBinReg0; b <= kBinBlock; ++b) {
         RowJob jb = j;
         jb.rows = rows + a.base[b];

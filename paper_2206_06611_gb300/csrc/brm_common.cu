@@ -35,15 +35,23 @@ __global__ void k_bin(BinArgs a) {
     int L = 0, bin = -1;
     int64_t np = 0;
     if (i < a.m) {
-        const int s = a.arp[i], e = a.arp[i + 1];
+        const int32_t *arp = a.arp, *acol = a.acol, *brp = a.brp;
+        int64_t li = i;
+        if (a.prods != nullptr) {
+            const ProdDesc &d = a.prods[a.prod_of[i]];
+            arp = d.arp; acol = d.acol; brp = d.brp;
+            li = i - d.row0;
+        }
+        const int s = arp[li], e = arp[li + 1];
         L = e - s;
         for (int p = s; p < e; ++p) {
-            const int k = a.acol[p];
-            np += a.brp[k + 1] - a.brp[k];
+            const int k = acol[p];
+            np += brp[k + 1] - brp[k];
         }
         // threads per row a register bin would need: enough for the products
-        // (32 per thread) and for the lists (8 per thread)
-        const int64_t need = max((np + kRegE - 1) / kRegE, (int64_t)(L + kRegListsPerThread - 1) / kRegListsPerThread);
+        // (E per thread) and for the lists (E/4 per thread)
+        const int E = a.reg_keys, EL = a.reg_keys / kRegKeysPerList;
+        const int64_t need = max((np + E - 1) / E, (int64_t)(L + EL - 1) / EL);
         if (np == 0) bin = kBinEmpty;
         else if (need <= a.reg_max_tpr) bin = kBinReg0 + (need <= 1 ? 0 : 32 - __clz((int)need - 1));
         else if (np <= a.warp_cap && L <= a.warp_cap) bin = kBinWarp;
@@ -90,11 +98,25 @@ __global__ void k_bin_scatter(BinArgs a) {
             const int64_t slot = (int64_t)base + __popc(mask & lanemask_lt());
             a.rows[a.base[b] + slot] = (int32_t)i;
             if (b == kBinLong && a.long_nprod) {
+                const int32_t *arp = a.arp;
+                int64_t li = i;
+                if (a.prods != nullptr) {
+                    const ProdDesc &d = a.prods[a.prod_of[i]];
+                    arp = d.arp;
+                    li = i - d.row0;
+                }
                 a.long_nprod[slot] = a.nprod[i];
-                a.long_L[slot] = a.arp[i + 1] - a.arp[i];
+                a.long_L[slot] = arp[li + 1] - arp[li];
             }
         }
     }
+}
+
+// Batched products: every stacked row learns its product.
+__global__ void k_fill_prod_of(const ProdDesc *prods, const int64_t *rows_of, int32_t *prod_of) {
+    const int p = blockIdx.x;
+    const int64_t r0 = prods[p].row0, n = rows_of[p];
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) prod_of[r0 + r] = p;
 }
 
 // Input check (CSR with strictly ascending in-range columns per row).
@@ -235,6 +257,14 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t st) {
     const int T = 256;
     const int64_t grid = (a.m + T - 1) / T;
     k_bin<<<(unsigned)grid, T, 0, st>>>(a);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_prod_of(const ProdDesc *prods, const int64_t *rows_of, int32_t count, int32_t *prod_of,
+                                cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_fill_prod_of<<<count, 256, 0, st>>>(prods, rows_of, prod_of);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -145,8 +145,20 @@ struct Buf {
     int32_t *off;
 };
 
+// One product of a batch (a device-side table; see brm_spgemm_batched): its
+// A and B and the first row of its block in the stacked row space.
+struct ProdDesc {
+    const int32_t *arp, *acol; const void *aval;
+    const int32_t *brp, *bcol; const void *bval;
+    int64_t row0;
+};
+
 // Everything a row kernel reads and writes.
 struct RowJob {
+    // batched products: row ids are rows of the stacked product and each row
+    // finds its own A and B through prod_of / prods (null: one product)
+    const ProdDesc *prods;
+    const int32_t *prod_of;
     const int32_t *arp, *acol; const void *aval;
     const int32_t *brp, *bcol; const void *bval;
     const int32_t *rows;        // row ids of this bin (or batch)
@@ -157,11 +169,47 @@ struct RowJob {
     int64_t *out_cnt;           // optional: receives each row's length
     unsigned int *err;          // set to 1 if a row's length disagrees with its slot
     int32_t exact;              // 1: a numeric row must fill its slot exactly (Precise)
+    int32_t reg_keys;           // register bins: keys per thread (8, 16 or 32)
+    int32_t reg_warps;          // register bins: warps per block
+    int32_t sym_hash;           // register bins, symbolic pass: 1 = count by hashing, 0 = by sorting
     // long rows only: per slot, the arena offset (bytes) and the product count
     char *arena;
     const int64_t *arena_off;
     const int64_t *slot_nprod;
 };
+
+// The inputs one output row needs: its row of A (columns and values from the
+// row's first entry on, L entries) and B.
+template <class In>
+struct RowIn {
+    const int32_t *acol;
+    const In *aval;
+    const int32_t *brp, *bcol;
+    const In *bval;
+    int L;
+};
+
+template <class In>
+__device__ __forceinline__ RowIn<In> row_in(const RowJob &j, int row) {
+    const int32_t *arp = j.arp, *acol = j.acol, *brp = j.brp, *bcol = j.bcol;
+    const void *aval = j.aval, *bval = j.bval;
+    int i = row;
+    if (j.prods != nullptr) {
+        const ProdDesc &d = j.prods[j.prod_of[row]];
+        arp = d.arp; acol = d.acol; aval = d.aval;
+        brp = d.brp; bcol = d.bcol; bval = d.bval;
+        i = row - (int)d.row0;
+    }
+    const int a0 = arp[i];
+    RowIn<In> r;
+    r.acol = acol + a0;
+    r.aval = static_cast<const In *>(aval) + a0;
+    r.brp = brp;
+    r.bcol = bcol;
+    r.bval = static_cast<const In *>(bval);
+    r.L = arp[i + 1] - a0;
+    return r;
+}
 
 // Largest t in [0, L) with off[t] <= p (off non-decreasing, off[0] = 0 <= p).
 __device__ __forceinline__ int find_last_le(const int32_t *off, int L, int p) {
@@ -424,10 +472,9 @@ __device__ __forceinline__ int merge_round(const G &g, int nl, const Buf<P> s, c
 template <class P, class G, int K, int UNR>
 __device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1) {
     using In = typename P::In;
-    const int a0 = j.arp[row];
-    const int L = j.arp[row + 1] - a0;
-    multiply_phase<P, G, UNR>(g, L, j.acol + a0, static_cast<const In *>(j.aval) + a0, j.brp, j.bcol,
-                              static_cast<const In *>(j.bval), b0, b1);
+    const RowIn<In> ri = row_in<In>(j, row);
+    const int L = ri.L;
+    multiply_phase<P, G, UNR>(g, L, ri.acol, ri.aval, ri.brp, ri.bcol, ri.bval, b0, b1);
     Buf<P> s = b0, d = b1;
     int nl = L;
     while (nl > 2) {

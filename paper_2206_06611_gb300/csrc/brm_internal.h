@@ -9,11 +9,13 @@
 namespace brm {
 
 struct RowJob;
+struct ProdDesc;
 
 // Row bins (by intermediate products nprod_i and list count L_i of a row):
 //   empty           nprod_i = 0 (the row of C is empty);
-//   register r=0..5 TPR = 2^r threads per row, nprod_i <= 32 * TPR and
-//                   L_i <= 8 * TPR, keys held in registers (brm_reg_rows.cuh);
+//   register r=0..5 TPR = 2^r threads per row holding E keys each (E = 8, 16
+//                   or 32): nprod_i <= E * TPR and L_i <= E/4 * TPR, keys sorted
+//                   in registers (brm_reg_rows.cuh);
 //   warp            one warp per row, shared-memory ping-pong (brm_rows.cuh);
 //   block           one thread block per row, shared-memory ping-pong;
 //   long            one thread block per row, device-memory ping-pong arena.
@@ -22,17 +24,20 @@ enum {
 };
 __host__ __device__ constexpr int reg_bin_tpr(int bin) { return 1 << (bin - kBinReg0); }
 
-// Capacities of the register bins: keys per thread, lists per thread.
-constexpr int kRegE = 32;
-constexpr int kRegListsPerThread = 8;
+// Register bins: keys per thread (E), lists per key, threads per row.
+constexpr int kRegKeysDefault = 16;
+constexpr int kRegKeysPerList = 4;    // a row may have up to E/4 lists per thread
 constexpr int kRegMaxTpr = 32;
-constexpr int kRegMaxNprod = kRegE * kRegMaxTpr;   // 1024
+constexpr int kRegMaxNprod = 32 * kRegMaxTpr;   // 1024 (E = 32; 512 with E = 16)
+constexpr int kRegWarpsDefault = 4;   // warps per block
 
-// Most columns B may have for a register bin with `tpr` threads per row: a
-// 32-bit key holds the column above the product's position in the row
-// (5 + log2(tpr) bits) and must stay below the all-ones padding key.
-__host__ __device__ constexpr int64_t reg_col_limit(int tpr) {
-    return (int64_t(1) << (27 - (tpr >= 32 ? 5 : tpr >= 16 ? 4 : tpr >= 8 ? 3 : tpr >= 4 ? 2 : tpr >= 2 ? 1 : 0))) - 1;
+// Most columns B may have for a register bin of `tpr` threads x `keys` keys:
+// a 32-bit key holds the column above the product's position in the row
+// (log2(tpr * keys) bits) and must stay below the all-ones padding key.
+__host__ __device__ constexpr int64_t reg_col_limit(int tpr, int keys) {
+    int b = 0;
+    for (int x = tpr * keys; x > 1; x >>= 1) ++b;
+    return (int64_t(1) << (32 - b)) - 1;
 }
 
 // Capacities of the shared-memory bins.
@@ -71,7 +76,10 @@ struct BinStats {
 struct BinArgs {
     int64_t m;
     const int32_t *arp, *acol, *brp;
+    const ProdDesc *prods;     // batched products (null: one product, arp/acol/brp)
+    const int32_t *prod_of;    // batched: product of every stacked row
     int32_t reg_max_tpr;   // largest register-bin TPR allowed (0: none)
+    int32_t reg_keys;      // keys per thread of the register bins (8, 16 or 32)
     int32_t warp_cap, block_cap, block_lcap;
     int64_t *nprod;        // optional, per row
     uint8_t *bin_of;       // optional, per row: its bin
@@ -85,6 +93,9 @@ struct BinArgs {
 };
 
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t st);
+// batched products: prod_of[row0[p] .. row0[p] + rows[p]) = p
+cudaError_t launch_fill_prod_of(const ProdDesc *prods, const int64_t *rows_of, int32_t count, int32_t *prod_of,
+                                cudaStream_t st);
 cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st);
 cudaError_t launch_validate(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rp, const int32_t *col,
                             BinStats *st, cudaStream_t stream);

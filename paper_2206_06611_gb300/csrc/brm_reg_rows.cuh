@@ -1,5 +1,5 @@
-// Register-resident BRMerge rows: nprod_i <= 32 * TPR and L_i <= 8 * TPR for
-// TPR = 1, 2, 4, ..., 32 threads per row.
+// Register-resident BRMerge rows: nprod_i <= E * TPR and L_i <= E/4 * TPR for
+// TPR = 1, 2, 4, ..., 32 threads per row and E = 8, 16 or 32 keys per thread.
 //
 // Algorithm 1 merges a row's L sorted lists two at a time in a binary tree and
 // adds the values of equal columns when their lists meet; the merging rounds
@@ -17,7 +17,7 @@
 //      the lists (so p grows with the list index); the rounded product
 //      A_ik * B_kj and its list index are parked in shared memory at p;
 //   2. the row's keys are sorted in registers by a bitonic network (TPR
-//      threads x 32 keys; stages across threads exchange keys by warp
+//      threads x E keys; stages across threads exchange keys by warp
 //      shuffles), which puts every column's products together in list order,
 //      the order the merging rounds produce;
 //   3. every run of equal columns is reduced in the tree order above (a run of
@@ -31,31 +31,60 @@
 
 namespace brm {
 
-constexpr int kRegWarps = 4;                 // warps per block
 constexpr int kRegU = 8;                     // products gathered per thread at a time
 constexpr uint32_t kKeyPad = 0xffffffffu;    // sorts after every real key
-// Per warp: a 32 x 33-word tile for the sorted keys (padded against bank
-// conflicts), which also holds the rows' list descriptors during the gather.
-constexpr size_t kRegStageBytes = 32 * 33 * 4 + 128;
 constexpr int kRegMaxDepth = 12;             // tree stack: log2(256 lists) + 1 levels suffice
 
 __host__ __device__ constexpr int ilog2_c(int x) { return x <= 1 ? 0 : 1 + ilog2_c(x >> 1); }
+__host__ __device__ constexpr size_t max_c(size_t a, size_t b) { return a > b ? a : b; }
 
-template <int TPR>
+// Per warp: an E x 33-word tile for the sorted keys (padded against bank
+// conflicts), which also holds the rows' list descriptors during the gather.
+__host__ __device__ constexpr size_t reg_stage_bytes(int E) {
+    return max_c((size_t)E * 33 * 4, (size_t)128 * E + 256);
+}
+
+template <int TPR, int E>
 struct RegCfg {
-    static constexpr int CAP = kRegE * TPR;                 // products per row
-    static constexpr int LCAP = kRegListsPerThread * TPR;   // lists per row
-    static constexpr int SB = 5 + ilog2_c(TPR);             // bits of the position in a key
+    static constexpr int CAP = E * TPR;                     // products per row
+    static constexpr int LCAP = (E / 4) * TPR;              // lists per row
+    static constexpr int SB = ilog2_c(CAP);                 // bits of the position in a key
+    static constexpr int LE = ilog2_c(E);
     static constexpr int RPW = 32 / TPR;                    // rows per warp
     static constexpr size_t DESC = 16 * (size_t)LCAP + 8;   // descriptor bytes per row
-    static_assert(RPW * DESC <= kRegStageBytes, "list descriptors must fit the staging tile");
+    static_assert((1 << LE) == E && E >= 8, "E must be a power of two");
+    static_assert(RPW * DESC <= reg_stage_bytes(E), "list descriptors must fit the staging tile");
 };
 
 // Shared memory of one warp: staging tile, then (numeric passes) the parked
-// products and their list indices for the warp's 32 * 32 positions.
+// products and their list indices for the warp's 32 * E positions.
 template <class P>
-__host__ __device__ constexpr size_t reg_warp_bytes() {
-    return kRegStageBytes + (P::kVal ? (sizeof(typename P::T) + sizeof(uint16_t)) * 32 * kRegE : 0);
+__host__ __device__ constexpr size_t reg_warp_bytes(int E) {
+    return reg_stage_bytes(E) + (P::kVal ? (sizeof(typename P::T) + sizeof(uint16_t)) * 32 * (size_t)E : 0);
+}
+
+// B is gathered many times over (every row of A that names k reads B_k*) and
+// C is written once: B's lines are loaded with an L2 evict-last policy and
+// C is stored with the streaming (evict-first) hint.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int32_t ld_keep(const int32_t *a, uint64_t pol) {
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *a, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const float *a, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
 }
 
 __device__ __forceinline__ void cmpswap(uint32_t &a, uint32_t &b) {
@@ -64,14 +93,14 @@ __device__ __forceinline__ void cmpswap(uint32_t &a, uint32_t &b) {
     b = hi;
 }
 
-// Ascending bitonic sort of the CAP = 32 * TPR keys of a row; thread t of the
-// row holds sorted positions 32 t .. 32 t + 31 in key[0..31] afterwards.  Each
-// merge stage k starts with a "flip" (position x against x ^ (k - 1)) and
+// Ascending bitonic sort of the CAP = E * TPR keys of a row; thread t of the
+// row holds sorted positions E t .. E t + E - 1 in key[0..E-1] afterwards.
+// Each merge stage k starts with a "flip" (position x against x ^ (k - 1)) and
 // continues with half cleaners (x against x ^ j), the smaller key always to
 // the lower position.
-template <int TPR>
-__device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[kRegE], int t) {
-    constexpr int E = kRegE, CAP = E * TPR;
+template <int TPR, int E>
+__device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[E], int t) {
+    constexpr int CAP = E * TPR, LE = ilog2_c(E);
     constexpr unsigned kFull = 0xffffffffu;
 #pragma unroll
     for (int k = 2; k <= CAP; k <<= 1) {
@@ -83,8 +112,8 @@ __device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[kRegE], int t) 
             }
         } else {
             // partner: element E-1-i of thread t ^ m
-            const int m = (k - 1) >> 5;
-            const bool lower = (t & (k >> 6)) == 0;
+            const int m = (k - 1) >> LE;
+            const bool lower = (t & (k >> (LE + 1))) == 0;
 #pragma unroll
             for (int i = 0; i < E / 2; ++i) {
                 const uint32_t o1 = __shfl_xor_sync(kFull, key[E - 1 - i], m);
@@ -100,7 +129,7 @@ __device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[kRegE], int t) 
                 for (int i = 0; i < E; ++i)
                     if ((i & jj) == 0) cmpswap(key[i], key[i | jj]);
             } else {
-                const int m = jj >> 5;
+                const int m = jj >> LE;
                 const bool lower = (t & m) == 0;
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
@@ -112,25 +141,26 @@ __device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[kRegE], int t) 
     }
 }
 
+template <int E>
 __device__ __forceinline__ uint32_t reg_sorted_key(const uint32_t *stage, int rowbase, int pos) {
-    return stage[(pos & 31) * 33 + rowbase + (pos >> 5)];
+    return stage[(pos & (E - 1)) * 33 + rowbase + (pos >> ilog2_c(E))];
 }
 
 // Tree-order sum of a run of equal columns starting at sorted position P0:
 // leaves in list order, two neighbours meet at the level bitlen(l1 ^ l2); a
 // stack of partial sums whose separating levels strictly decrease is reduced
 // whenever the next leaf is separated by a higher level.
-template <class P, int SB>
+template <class P, int SB, int E>
 __device__ __noinline__ typename P::T reg_tree_reduce(const uint32_t *stage, int rowbase, int P0, int N,
                                                       const typename P::T *vals, const uint16_t *lidx) {
     using T = typename P::T;
     constexpr uint32_t SMASK = (1u << SB) - 1u;
     T V[kRegMaxDepth];
     int G[kRegMaxDepth];
-    const uint32_t c = reg_sorted_key(stage, rowbase, P0) >> SB;
+    const uint32_t c = reg_sorted_key<E>(stage, rowbase, P0) >> SB;
     int nv = 0, prev_l = 0;
     for (int pos = P0; pos < N; ++pos) {
-        const uint32_t kk = reg_sorted_key(stage, rowbase, pos);
+        const uint32_t kk = reg_sorted_key<E>(stage, rowbase, pos);
         if ((kk >> SB) != c) break;
         const int p = (int)(kk & SMASK);
         const int l = lidx[p];
@@ -156,20 +186,19 @@ __device__ __noinline__ typename P::T reg_tree_reduce(const uint32_t *stage, int
     return V[0];
 }
 
-template <class P, int TPR>
-__global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
-    using Cf = RegCfg<TPR>;
+template <class P, int TPR, int E>
+__global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
+    using Cf = RegCfg<TPR, E>;
     using In = typename P::In;
     using T = typename P::T;
     using Out = typename P::Out;
-    constexpr int E = kRegE;
     constexpr int SB = P::kVal ? Cf::SB : 0;   // the symbolic pass sorts bare columns
     constexpr uint32_t SMASK = (1u << Cf::SB) - 1u;
     constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int rho = lane / TPR, t = lane % TPR, rowbase = rho * TPR;
-    unsigned char *wb = smem + (size_t)wid * reg_warp_bytes<P>();
+    unsigned char *wb = smem + (size_t)wid * reg_warp_bytes<P>(E);
     uint32_t *stage = reinterpret_cast<uint32_t *>(wb);
     unsigned char *desc = wb + (size_t)rho * Cf::DESC;
     In *d_a = reinterpret_cast<In *>(desc);
@@ -178,19 +207,19 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
     T *vals = nullptr;
     uint16_t *lidx = nullptr;
     if constexpr (P::kVal) {
-        vals = reinterpret_cast<T *>(wb + kRegStageBytes) + rho * Cf::CAP;
-        lidx = reinterpret_cast<uint16_t *>(wb + kRegStageBytes + sizeof(T) * 32 * E) + rho * Cf::CAP;
+        vals = reinterpret_cast<T *>(wb + reg_stage_bytes(E)) + rho * Cf::CAP;
+        lidx = reinterpret_cast<uint16_t *>(wb + reg_stage_bytes(E) + sizeof(T) * 32 * E) + rho * Cf::CAP;
     }
-    const In *aval = static_cast<const In *>(j.aval);
-    const In *bval = static_cast<const In *>(j.bval);
-    const int stride = gridDim.x * kRegWarps * Cf::RPW;
+    const uint64_t keep = l2_keep_policy();
+    const int stride = gridDim.x * nwarps * Cf::RPW;
 
-    for (int r0 = (blockIdx.x * kRegWarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
+    for (int r0 = (blockIdx.x * nwarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
         const int slot = r0 + rho;
         const bool has_row = slot < j.count;
         const int row = has_row ? j.rows[slot] : 0;
-        const int a0 = has_row ? j.arp[row] : 0;
-        const int L = has_row ? j.arp[row + 1] - a0 : 0;
+        RowIn<In> ri{};
+        if (has_row) ri = row_in<In>(j, row);
+        const int L = has_row ? ri.L : 0;
 
         // ---- list descriptors: start of B_k*, A_ik, and the list ends ------
         int carry = 0;
@@ -198,11 +227,11 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
             const int l = c0 + t;
             int len = 0;
             if (l < L) {
-                const int k = j.acol[a0 + l];
-                const int q0 = j.brp[k];
-                len = j.brp[k + 1] - q0;
+                const int k = ri.acol[l];
+                const int q0 = ri.brp[k];
+                len = ri.brp[k + 1] - q0;
                 d_q0[l] = q0;
-                if constexpr (P::kVal) d_a[l] = aval[a0 + l];
+                if constexpr (P::kVal) d_a[l] = ri.aval[l];
             }
             int incl = len;
 #pragma unroll
@@ -249,8 +278,8 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
                     c[u] = 0;
                     v[u] = In();
                     if (q[u] >= 0) {
-                        c[u] = __ldg(j.bcol + q[u]);
-                        if constexpr (P::kVal) v[u] = __ldg(bval + q[u]);
+                        c[u] = ld_keep(ri.bcol + q[u], keep);
+                        if constexpr (P::kVal) v[u] = ld_keep(ri.bval + q[u], keep);
                     }
                 }
 #pragma unroll
@@ -265,7 +294,7 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
         }
 
         // ---- accumulating phase: sort, then runs of equal columns -----------
-        reg_bitonic_sort<TPR>(key, t);
+        reg_bitonic_sort<TPR, E>(key, t);
 
         if constexpr (!P::kVal) {
             // symbolic: distinct columns of the row
@@ -292,26 +321,28 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
             const unsigned gmask = (TPR == 32) ? kFull : (((1u << TPR) - 1u) << rowbase);
             const unsigned lt = (1u << lane) - 1u;
             int count = 0;
+            // sorted position pos = jj * TPR + t: consecutive threads write
+            // consecutive elements of the row
             for (int jj = 0; __any_sync(kFull, jj * TPR < N); ++jj) {
                 const int pos = jj * TPR + t;
                 bool live = false;
                 uint32_t kk = kKeyPad;
                 if (pos < N) {
-                    kk = reg_sorted_key(stage, rowbase, pos);
-                    live = pos == 0 || (reg_sorted_key(stage, rowbase, pos - 1) >> SB) != (kk >> SB);
+                    kk = reg_sorted_key<E>(stage, rowbase, pos);
+                    live = pos == 0 || (reg_sorted_key<E>(stage, rowbase, pos - 1) >> SB) != (kk >> SB);
                 }
                 const unsigned msk = __ballot_sync(kFull, live) & gmask;
                 if (live) {
                     const int w = count + __popc(msk & lt);
                     const uint32_t c = kk >> SB;
                     T v;
-                    if (pos + 1 >= N || (reg_sorted_key(stage, rowbase, pos + 1) >> SB) != c)
+                    if (pos + 1 >= N || (reg_sorted_key<E>(stage, rowbase, pos + 1) >> SB) != c)
                         v = vals[kk & SMASK];
                     else
-                        v = reg_tree_reduce<P, SB>(stage, rowbase, pos, N, vals, lidx);
+                        v = reg_tree_reduce<P, SB, E>(stage, rowbase, pos, N, vals, lidx);
                     if (w < cap) {
-                        ocol[w] = (int32_t)c;
-                        oval[w] = P::fin(v);
+                        __stcs(ocol + w, (int32_t)c);
+                        __stcs(oval + w, P::fin(v));
                     }
                 }
                 count += __popc(msk);
@@ -325,33 +356,159 @@ __global__ void __launch_bounds__(kRegWarps * 32) k_rows_reg(RowJob j) {
     }
 }
 
-template <class P, int TPR>
-cudaError_t launch_reg_t(const RowJob &j, cudaStream_t st, int sms) {
-    const size_t sm = kRegWarps * reg_warp_bytes<P>();
-    auto kern = k_rows_reg<P, TPR>;
+// ---------------------------------------------------------------------------
+// Symbolic pass of the register bins by hashing (option symbolic_hash), as the
+// paper's BRMerge-Precise does its symbolic step (Section III-D-2; on GB300
+// the register sort is faster): every column of the row's lists is
+// inserted into a shared-memory open-addressing table of 2 * CAP slots
+// (multiplicative hash, linear probing, load factor <= 1/2) and the row's
+// nnz is the number of first insertions.  The count is an integer, so the
+// method of counting does not change the result.
+// ---------------------------------------------------------------------------
+template <int E>
+__host__ __device__ constexpr size_t hash_warp_bytes() {
+    return reg_stage_bytes(E) + (size_t)2 * 32 * E * sizeof(int32_t);
+}
+
+template <int TPR, int E>
+__global__ void __launch_bounds__(256) k_sym_hash(RowJob j) {
+    using Cf = RegCfg<TPR, E>;
+    constexpr int HS = 2 * Cf::CAP;                   // table slots per row
+    constexpr int HB = ilog2_c(HS);
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int rho = lane / TPR, t = lane % TPR;
+    unsigned char *wb = smem + (size_t)wid * hash_warp_bytes<E>();
+    unsigned char *desc = wb + (size_t)rho * Cf::DESC;
+    int32_t *d_q0 = reinterpret_cast<int32_t *>(desc + 8 * Cf::LCAP);
+    int32_t *d_off = reinterpret_cast<int32_t *>(desc + 12 * Cf::LCAP);
+    int32_t *tab = reinterpret_cast<int32_t *>(wb + reg_stage_bytes(E)) + rho * HS;
+    const uint64_t keep = l2_keep_policy();
+    const int stride = gridDim.x * nwarps * Cf::RPW;
+
+    for (int r0 = (blockIdx.x * nwarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
+        const int slot = r0 + rho;
+        const bool has_row = slot < j.count;
+        const int row = has_row ? j.rows[slot] : 0;
+        RowIn<float> ri{};
+        if (has_row) ri = row_in<float>(j, row);
+        const int L = has_row ? ri.L : 0;
+        int carry = 0;
+        for (int c0 = 0; __any_sync(kFull, c0 < L); c0 += TPR) {
+            const int l = c0 + t;
+            int len = 0;
+            if (l < L) {
+                const int k = ri.acol[l];
+                const int q0 = ri.brp[k];
+                len = ri.brp[k + 1] - q0;
+                d_q0[l] = q0;
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < TPR; d <<= 1) {
+                const int u = __shfl_up_sync(kFull, incl, d, TPR);
+                if (t >= d) incl += u;
+            }
+            if (l < L) d_off[l + 1] = carry + incl;
+            carry += __shfl_sync(kFull, incl, TPR - 1, TPR);
+        }
+        if (t == 0) d_off[0] = 0;
+        const int N = carry;
+#pragma unroll 4
+        for (int x = t; x < HS; x += TPR) tab[x] = -1;
+        __syncwarp();
+        // all of this thread's columns in flight at once
+        int32_t c[E];
+        {
+            int l = 0;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int p = i * TPR + t;
+                c[i] = -1;
+                if (p < N) {
+                    while (d_off[l + 1] <= p) ++l;
+                    c[i] = ld_keep(ri.bcol + d_q0[l] + (p - d_off[l]), keep);
+                }
+            }
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            if (c[i] >= 0) {
+                unsigned h = ((uint32_t)c[i] * 0x9E3779B1u) >> (32 - HB);
+                while (true) {
+                    const int old = atomicCAS(tab + h, -1, c[i]);
+                    if (old == -1) { ++cnt; break; }
+                    if (old == c[i]) break;
+                    h = (h + 1) & (HS - 1);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 1; d < TPR; d <<= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+        if (has_row && t == 0 && j.out_cnt != nullptr) j.out_cnt[row] = cnt;
+        __syncwarp();   // the table and the descriptors are reused by the next rows
+    }
+}
+
+template <int TPR, int E>
+cudaError_t launch_sym_hash_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
+    const size_t sm = (size_t)warps * hash_warp_bytes<E>();
+    auto kern = k_sym_hash<TPR, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRegWarps * 32, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm);
     if (e != cudaSuccess) return e;
-    const int rows_per_block = kRegWarps * RegCfg<TPR>::RPW;
+    const int rows_per_block = warps * RegCfg<TPR, E>::RPW;
     const int need = (j.count + rows_per_block - 1) / rows_per_block;
     const int grid = max(1, min(need, sms * max(occ, 1)));
-    kern<<<grid, kRegWarps * 32, sm, st>>>(j);
+    kern<<<grid, warps * 32, sm, st>>>(j);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
+template <class P, int TPR, int E>
+cudaError_t launch_reg_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
+    if constexpr (!P::kVal) {
+        if (j.sym_hash) return launch_sym_hash_t<TPR, E>(j, st, sms, warps);
+    }
+    const size_t sm = (size_t)warps * reg_warp_bytes<P>(E);
+    auto kern = k_rows_reg<P, TPR, E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm);
+    if (e != cudaSuccess) return e;
+    const int rows_per_block = warps * RegCfg<TPR, E>::RPW;
+    const int need = (j.count + rows_per_block - 1) / rows_per_block;
+    const int grid = max(1, min(need, sms * max(occ, 1)));
+    kern<<<grid, warps * 32, sm, st>>>(j);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+template <class P, int E>
+cudaError_t launch_reg_e(int tpr, const RowJob &j, cudaStream_t st, int sms, int warps) {
+    switch (tpr) {
+        case 1: return launch_reg_t<P, 1, E>(j, st, sms, warps);
+        case 2: return launch_reg_t<P, 2, E>(j, st, sms, warps);
+        case 4: return launch_reg_t<P, 4, E>(j, st, sms, warps);
+        case 8: return launch_reg_t<P, 8, E>(j, st, sms, warps);
+        case 16: return launch_reg_t<P, 16, E>(j, st, sms, warps);
+        default: return launch_reg_t<P, 32, E>(j, st, sms, warps);
+    }
+}
+
+// Register bin `tpr` with `keys` (8, 16 or 32) keys per thread and `warps`
+// warps per block.
 template <class P>
 cudaError_t launch_reg_rows(int tpr, const RowJob &j, cudaStream_t st, int sms) {
-    switch (tpr) {
-        case 1: return launch_reg_t<P, 1>(j, st, sms);
-        case 2: return launch_reg_t<P, 2>(j, st, sms);
-        case 4: return launch_reg_t<P, 4>(j, st, sms);
-        case 8: return launch_reg_t<P, 8>(j, st, sms);
-        case 16: return launch_reg_t<P, 16>(j, st, sms);
-        default: return launch_reg_t<P, 32>(j, st, sms);
-    }
+    const int warps = (j.reg_warps >= 1 && j.reg_warps <= 8) ? j.reg_warps : 4;
+    if (j.reg_keys == 8) return launch_reg_e<P, 8>(tpr, j, st, sms, warps);
+    if (j.reg_keys == 16) return launch_reg_e<P, 16>(tpr, j, st, sms, warps);
+    return launch_reg_e<P, 32>(tpr, j, st, sms, warps);
 }
 
 }  // namespace brm

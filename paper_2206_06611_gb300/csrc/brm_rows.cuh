@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
     for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
         const int row = j.rows[r];
         const int64_t n = j.slot_nprod[r];
-        const int L = j.arp[row + 1] - j.arp[row];
+        const int L = row_in<typename P::In>(j, row).L;
         unsigned char *p = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[r];
         const LongLayout lay = long_layout<P>(n, L);
         Buf<P> b0, b1;

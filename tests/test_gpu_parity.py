@@ -98,12 +98,16 @@ def test_bins_small_thresholds():
     ref = oracle.alg1(A, B)
     for rcap, wcap, bcap in ((-1, 8, 64), (-1, 32, 32), (-1, 1, 2), (64, 0, 0), (256, 0, 0), (-1, 0, 0)):
         assert_rows_exact(run(A, B, reg_max_nprod=rcap, warp_max_nprod=wcap, block_max_nprod=bcap), ref)
+    for keys in (8, 16, 32):
+        for sym_hash in (False, True):
+            assert_rows_exact(run(A, B, reg_keys=keys, symbolic_hash=sym_hash), ref)
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
 def test_register_bins_every_size(mode, dtype, comp):
-    """Rows of 1..1024 products and 1..256 lists (every register bin, their
-    capacity edges, duplicate-heavy and duplicate-free rows)."""
+    """Rows of 1..1024 products and 1..256 lists (every register bin with 8,
+    16 and 32 keys per thread, their capacity edges, duplicate-heavy and
+    duplicate-free rows)."""
     k, n = 3000, 2500
     B = I.erdos_renyi(k, 4, seed=31, ncols=n)
     Bd = I.erdos_renyi(k, 4, seed=32, ncols=40)          # few columns: long runs of duplicates
@@ -119,8 +123,9 @@ def test_register_bins_every_size(mode, dtype, comp):
         acol = np.concatenate(rows).astype(np.int32)
         A = I.CSR(len(rows), k, arp.astype(np.int32), acol, I.rand_sym(35, 1, np.arange(len(acol))))
         ref = oracle.alg1(A, Bm, prec=mode)
-        assert_rows_exact(run(A, Bm, "precise", dtype, comp), ref)
-        assert_rows_exact(run(A, Bm, "upper", dtype, comp), ref)
+        for keys in (8, 16, 32):
+            assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys), ref)
+            assert_rows_exact(run(A, Bm, "upper", dtype, comp, reg_keys=keys), ref)
 
 
 def test_register_bins_wide_B():
@@ -213,9 +218,10 @@ def test_trace_counts_launches():
     brm.brm_trace_enable(was)
     assert brm.brm_kernel_launches() > n0
     # every row of the 32 x 32 Laplacian squared has <= 25 products and <= 5
-    # lists: all in the one-thread-per-row register bin
-    assert t["numeric_reg"][1] == 1 and t["numeric_reg"][0] > 0
-    assert t["bin"][1] == 2 and t["symbolic_reg"][1] == 1 and t["numeric_warp"][1] == 0
+    # lists: all in the register bins of one or two threads per row
+    assert 1 <= t["numeric_reg"][1] <= 2 and t["numeric_reg"][0] > 0
+    assert t["bin"][1] == 2 and t["symbolic_reg"][1] == t["numeric_reg"][1]
+    assert t["numeric_warp"][1] == 0 and t["numeric_block"][1] == 0 and t["numeric_long"][1] == 0
 
 
 # --------------------------------------------------------------------------
