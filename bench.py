@@ -57,6 +57,27 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """x maximised over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(products_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job GFLOP/s: every rank does its own product (weak scaling); the
+    slowest rank's time counts."""
+    return world * 2.0 * products_per_rank * steps / (ms_max * 1e-3) / 1e9
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank multiplies its own independent matrix (no data-path collective)."""
+    return I.DEFAULT_SEED + rank
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,7 +219,7 @@ def run_gpu(args):
             dist.barrier()
 
     # every rank multiplies its own independent matrix (weak scaling)
-    A = I.erdos_renyi(1 << 20, 16, seed=I.DEFAULT_SEED + rank)
+    A = I.erdos_renyi(1 << 20, 16, seed=rank_seed(rank))
     vbytes = 8
     dA = brm.to_device(A, device=f"cuda:{dev}")
     st = torch.cuda.current_stream()
@@ -232,12 +253,8 @@ def run_gpu(args):
     trace = brm.brm_trace_read()
     brm.brm_trace_enable(False)
     clk = clocks.stop() if clocks else None
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * 2.0 * nprod_total * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = reduce_max(ms, dist, f"cuda:{dev}")
+    value = job_gflops(nprod_total, world, args.steps, ms_max)
 
     # ---- end to end: host buffers, copies inside the timed region ----------
     hA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
@@ -268,11 +285,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
     barrier()
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * 2.0 * nprod_total * e_steps / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = reduce_max(e2e_ms, dist, f"cuda:{dev}")
+    e2e_value = job_gflops(nprod_total, world, e_steps, e2e_ms)
 
     if rank != 0:
         if dist is not None:

@@ -110,6 +110,11 @@ typedef struct {
  *   reg_keys       8, 16 or 32 (default 16; other values give 16);
  *   reg_warps      warps per block of the register-bin kernels, 1..8
  *                  (default 4);
+ *   reg_top        1 (default): with reg_keys < 32, rows of up to
+ *                  64 * reg_keys products (and 16 * reg_keys lists) beyond
+ *                  the register bins still take a register kernel, with 32
+ *                  threads of 2 * reg_keys keys; 0: they take the shared-
+ *                  memory kernels;
  *   symbolic_hash  register bins count a row's distinct columns in the
  *                  symbolic pass with the numeric pass's sorting network on
  *                  bare columns (0, default) or by hashing into a
@@ -134,6 +139,7 @@ typedef struct {
     int32_t reg_keys;
     int32_t reg_warps;
     int32_t symbolic_hash;
+    int32_t reg_top;
     size_t arena_bytes;
 } brm_options;
 

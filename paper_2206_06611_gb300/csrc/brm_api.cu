@@ -206,6 +206,7 @@ brm_options resolve(const brm_options *o) {
     if (r.reg_keys != 8 && r.reg_keys != 16 && r.reg_keys != 32) r.reg_keys = kRegKeysDefault;
     if (r.reg_warps < 1 || r.reg_warps > 8) r.reg_warps = kRegWarpsDefault;
     if (r.reg_max_nprod == 0 || r.reg_max_nprod > r.reg_keys * kRegMaxTpr) r.reg_max_nprod = r.reg_keys * kRegMaxTpr;
+    r.reg_top = r.reg_top != 0 ? 1 : 0;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -217,6 +218,13 @@ int reg_max_tpr(const brm_options &o, int64_t bcols) {
     for (int tpr = 1; tpr <= kRegMaxTpr; tpr <<= 1)
         if (o.reg_keys * tpr <= o.reg_max_nprod && bcols <= reg_col_limit(tpr, o.reg_keys)) best = tpr;
     return best;
+}
+
+// The top register bin (32 threads x 2 reg_keys keys): only below 32 keys, when
+// the other register bins are all usable and reg_max_nprod was not lowered.
+int reg_top_ok(const brm_options &o, int64_t bcols) {
+    return o.reg_keys < 32 && reg_max_tpr(o, bcols) == kRegMaxTpr && o.reg_max_nprod >= 32 * o.reg_keys &&
+           o.reg_top && bcols <= reg_col_limit(32, 2 * o.reg_keys);
 }
 
 // Result of the binning step.
@@ -272,6 +280,7 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
     a.prod_of = src.prod_of;
     a.reg_max_tpr = reg_max_tpr(o, src.bcols);
     a.reg_keys = o.reg_keys;
+    a.reg_top = reg_top_ok(o, src.bcols);
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;
@@ -800,6 +809,7 @@ void brm_options_default(brm_options *o) {
     o->reg_max_nprod = kRegMaxNprod;
     o->reg_keys = kRegKeysDefault;
     o->reg_warps = kRegWarpsDefault;
+    o->reg_top = 1;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
 }
@@ -1149,6 +1159,7 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     a.brp = B->row_ptr;
     a.reg_max_tpr = reg_max_tpr(o, B->cols);
     a.reg_keys = o.reg_keys;
+    a.reg_top = reg_top_ok(o, B->cols);
     a.warp_cap = o.warp_max_nprod;
     a.block_cap = o.block_max_nprod;
     a.block_lcap = kBlockLCap;

@@ -54,6 +54,7 @@ __global__ void k_bin(BinArgs a) {
         const int64_t need = max((np + E - 1) / E, (int64_t)(L + EL - 1) / EL);
         if (np == 0) bin = kBinEmpty;
         else if (need <= a.reg_max_tpr) bin = kBinReg0 + (need <= 1 ? 0 : 32 - __clz((int)need - 1));
+        else if (a.reg_top && np <= 64 * E && L <= 16 * E) bin = kBinRegTop;
         else if (np <= a.warp_cap && L <= a.warp_cap) bin = kBinWarp;
         else if (np <= a.block_cap && L <= a.block_lcap) bin = kBinBlock;
         else bin = kBinLong;
@@ -67,16 +68,27 @@ __global__ void k_bin(BinArgs a) {
         if (mask != 0u && lane == __ffs(mask) - 1) atomicAdd(&a.st->count[b], (unsigned long long)__popc(mask));
     }
     unsigned long long sum = (unsigned long long)np, mx = (unsigned long long)np, ml = (unsigned long long)L;
+    unsigned long long rs = (bin >= kBinReg0 && bin < kBinReg0 + kNumRegBins) ? (unsigned long long)np : 0ull;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         sum += __shfl_down_sync(kFull, sum, d);
+        rs += __shfl_down_sync(kFull, rs, d);
         mx = max(mx, (unsigned long long)__shfl_down_sync(kFull, mx, d));
         ml = max(ml, (unsigned long long)__shfl_down_sync(kFull, ml, d));
     }
     if (lane == 0) {
         if (sum) atomicAdd(&a.st->total_nprod, sum);
+        if (rs) atomicAdd(&a.st->reg_nprod, rs);
         atomicMax(&a.st->max_nprod, mx);
         atomicMax(&a.st->max_L, ml);
+    }
+}
+
+__global__ void k_reg_nprod(int64_t m, const uint8_t *bin_of, const int64_t *nprod, int64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) {
+        const int b = bin_of[i];
+        out[i] = (b >= kBinReg0 && b < kBinReg0 + kNumRegBins) ? nprod[i] : 0;
     }
 }
 
@@ -274,6 +286,14 @@ cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st) {
     const int T = 256;
     const int64_t grid = (a.m + T - 1) / T;
     k_bin_scatter<<<(unsigned)grid, T, 0, st>>>(a);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_nprod(int64_t m, const uint8_t *bin_of, const int64_t *nprod, int64_t *out, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    const int T = 256;
+    k_reg_nprod<<<(unsigned)((m + T - 1) / T), T, 0, st>>>(m, bin_of, nprod, out);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

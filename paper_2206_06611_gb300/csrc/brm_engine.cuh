@@ -40,6 +40,7 @@ constexpr int32_t kColEnd = 0x7fffffff;   // larger than any column index (< 2^3
 struct PF64 {
     using In = double; using T = double; using Out = double;
     static constexpr bool kVal = true;
+    static constexpr bool kPerm = false;
     __device__ static __forceinline__ T mul(In a, In b) { return __dmul_rn(a, b); }
     __device__ static __forceinline__ T add(T x, T y) { return __dadd_rn(x, y); }
     __device__ static __forceinline__ Out fin(T x) { return x; }
@@ -48,6 +49,7 @@ struct PF64 {
 struct PF32 {
     using In = float; using T = float; using Out = float;
     static constexpr bool kVal = true;
+    static constexpr bool kPerm = false;
     __device__ static __forceinline__ T mul(In a, In b) { return __fmul_rn(a, b); }
     __device__ static __forceinline__ T add(T x, T y) { return __fadd_rn(x, y); }
     __device__ static __forceinline__ Out fin(T x) { return x; }
@@ -60,6 +62,7 @@ struct PF32 {
 struct PF32C {
     using In = float; using T = float2; using Out = float;
     static constexpr bool kVal = true;
+    static constexpr bool kPerm = false;
     __device__ static __forceinline__ T mul(In a, In b) { return make_float2(__fmul_rn(a, b), 0.0f); }
     __device__ static __forceinline__ T add(T x, T y) {
         const float s = __fadd_rn(x.x, y.x);
@@ -74,10 +77,23 @@ struct PF32C {
 struct PIdx {
     using In = float; using T = float; using Out = float;   // never loaded or stored
     static constexpr bool kVal = false;
+    static constexpr bool kPerm = false;
     __device__ static __forceinline__ T mul(In, In) { return 0.0f; }
     __device__ static __forceinline__ T add(T, T) { return 0.0f; }
     __device__ static __forceinline__ Out fin(T) { return 0.0f; }
 };
+
+// The symbolic pass that also records, for every register-bin row, the order
+// in which its merge tree leaves the products: their positions sorted by
+// (column, list), with the start of every run of equal columns marked.
+struct PPerm : PIdx {
+    static constexpr bool kPerm = true;
+};
+
+// Entries of a recorded row order (one 16-bit word per product).
+constexpr uint32_t kPermPos = 0x03ffu;     // the product's position in the row (< 1024)
+constexpr uint32_t kPermStart = 0x8000u;   // first element of a run of equal columns
+constexpr uint32_t kPermMulti = 0x4000u;   // ... of a run of two or more elements
 
 // ---------------------------------------------------------------------------
 // Thread groups.
@@ -172,6 +188,10 @@ struct RowJob {
     int32_t reg_keys;           // register bins: keys per thread (8, 16 or 32)
     int32_t reg_warps;          // register bins: warps per block
     int32_t sym_hash;           // register bins, symbolic pass: 1 = count by hashing, 0 = by sorting
+    // register bins: the rows' recorded orders (written by the symbolic pass,
+    // applied by the numeric pass); null: the numeric pass sorts by itself
+    uint16_t *perm;
+    const int64_t *perm_off;    // per row: where its order starts in perm
     // long rows only: per slot, the arena offset (bytes) and the product count
     char *arena;
     const int64_t *arena_off;

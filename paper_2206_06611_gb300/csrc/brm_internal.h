@@ -19,10 +19,13 @@ struct ProdDesc;
 //   warp            one warp per row, shared-memory ping-pong (brm_rows.cuh);
 //   block           one thread block per row, shared-memory ping-pong;
 //   long            one thread block per row, device-memory ping-pong arena.
+//   register top    (only when E < 32) 32 threads holding 2E keys each, for
+//                   rows just above the largest register bin;
 enum {
-    kBinEmpty = 0, kBinReg0 = 1, kNumRegBins = 6, kBinWarp = kBinReg0 + kNumRegBins, kBinBlock, kBinLong, kNumBins
+    kBinEmpty = 0, kBinReg0 = 1, kNumRegBins = 7, kBinRegTop = kBinReg0 + 6, kBinWarp = kBinReg0 + kNumRegBins,
+    kBinBlock, kBinLong, kNumBins
 };
-__host__ __device__ constexpr int reg_bin_tpr(int bin) { return 1 << (bin - kBinReg0); }
+__host__ __device__ constexpr int reg_bin_tpr(int bin) { return bin == kBinRegTop ? 32 : 1 << (bin - kBinReg0); }
 
 // Register bins: keys per thread (E), lists per key, threads per row.
 constexpr int kRegKeysDefault = 16;
@@ -68,6 +71,7 @@ struct BinStats {
     unsigned long long max_L;
     unsigned long long bad;   // validation: nonzero if an input is malformed
     unsigned long long cursor[kNumBins];   // fill level of each bin during the scatter
+    unsigned long long reg_nprod;          // products of the rows in register bins
 };
 
 // Binning in two passes: k_bin classifies every row (bin_of, counts); after
@@ -80,6 +84,7 @@ struct BinArgs {
     const int32_t *prod_of;    // batched: product of every stacked row
     int32_t reg_max_tpr;   // largest register-bin TPR allowed (0: none)
     int32_t reg_keys;      // keys per thread of the register bins (8, 16 or 32)
+    int32_t reg_top;       // 1: the top register bin (32 threads x 2 reg_keys) is allowed
     int32_t warp_cap, block_cap, block_lcap;
     int64_t *nprod;        // optional, per row
     uint8_t *bin_of;       // optional, per row: its bin
@@ -97,6 +102,8 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t st);
 cudaError_t launch_fill_prod_of(const ProdDesc *prods, const int64_t *rows_of, int32_t count, int32_t *prod_of,
                                 cudaStream_t st);
 cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st);
+// out[i] = nprod[i] if row i is in a register bin, else 0
+cudaError_t launch_reg_nprod(int64_t m, const uint8_t *bin_of, const int64_t *nprod, int64_t *out, cudaStream_t st);
 cudaError_t launch_validate(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rp, const int32_t *col,
                             BinStats *st, cudaStream_t stream);
 // exclusive scan of in[0..n) into out[0..n] (out[n] = total); tmp needs

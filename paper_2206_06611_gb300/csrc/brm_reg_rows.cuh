@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
     using In = typename P::In;
     using T = typename P::T;
     using Out = typename P::Out;
-    constexpr int SB = P::kVal ? Cf::SB : 0;   // the symbolic pass sorts bare columns
+    // the symbolic pass sorts bare columns unless it records the rows' order
+    constexpr int SB = (P::kVal || P::kPerm) ? Cf::SB : 0;
     constexpr uint32_t SMASK = (1u << Cf::SB) - 1u;
     constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -296,7 +297,31 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
         // ---- accumulating phase: sort, then runs of equal columns -----------
         reg_bitonic_sort<TPR, E>(key, t);
 
-        if constexpr (!P::kVal) {
+        if constexpr (P::kPerm) {
+            // symbolic, recording the order: every sorted position gets its
+            // product's position and the run marks; the runs are counted
+            __syncwarp();   // every lane is done with the descriptors (same memory)
+#pragma unroll
+            for (int i = 0; i < E; ++i) stage[i * 33 + lane] = key[i];
+            __syncwarp();
+            uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
+            int cnt = 0;
+            for (int jj = 0; __any_sync(kFull, jj * TPR < N); ++jj) {
+                const int pos = jj * TPR + t;
+                if (pos < N) {
+                    const uint32_t kk = reg_sorted_key<E>(stage, rowbase, pos);
+                    const uint32_t c = kk >> SB;
+                    const bool start = pos == 0 || (reg_sorted_key<E>(stage, rowbase, pos - 1) >> SB) != c;
+                    const bool multi =
+                        start && pos + 1 < N && (reg_sorted_key<E>(stage, rowbase, pos + 1) >> SB) == c;
+                    pr[pos] = (uint16_t)((kk & SMASK) | (start ? kPermStart : 0u) | (multi ? kPermMulti : 0u));
+                    cnt += start ? 1 : 0;
+                }
+            }
+#pragma unroll
+            for (int d = 1; d < TPR; d <<= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+            if (has_row && t == 0 && j.out_cnt != nullptr) j.out_cnt[row] = cnt;
+        } else if constexpr (!P::kVal) {
             // symbolic: distinct columns of the row
             const uint32_t before = __shfl_up_sync(kFull, key[E - 1], 1, TPR);
             int cnt = 0;
@@ -469,10 +494,210 @@ cudaError_t launch_sym_hash_t(const RowJob &j, cudaStream_t st, int sms, int war
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Numeric pass of the register bins from a recorded order (BRMerge-Precise,
+// whose symbolic pass sorted every row already): the products are formed in
+// list order and parked at their positions, then read in the recorded order;
+// a run of one is its product, a longer run is reduced in the tree order of
+// Algorithm 1 (list indices of its elements, as in reg_tree_reduce).  The
+// result is the one of the sorting kernel, without sorting again.
+// ---------------------------------------------------------------------------
+template <int E, class P>
+__host__ __device__ constexpr size_t perm_warp_bytes() {
+    return reg_stage_bytes(E) + (sizeof(typename P::T) + sizeof(int32_t) + sizeof(uint8_t)) * 32 * (size_t)E;
+}
+
+template <class P>
+__device__ __noinline__ typename P::T perm_tree_reduce(const uint16_t *pr, int P0, int N, const typename P::T *vals,
+                                                       const uint8_t *lidx) {
+    using T = typename P::T;
+    T V[kRegMaxDepth];
+    int G[kRegMaxDepth];
+    int nv = 0, prev_l = 0;
+    for (int pos = P0; pos < N; ++pos) {
+        const uint32_t pe = pr[pos];
+        if (pos > P0 && (pe & kPermStart)) break;
+        const int p = (int)(pe & kPermPos);
+        const int l = lidx[p];
+        if (nv > 0) {
+            const int d = 32 - __clz(prev_l ^ l);
+            while (nv > 1 && G[nv - 1] < d) {
+                V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+                --nv;
+            }
+            G[nv] = d;
+        }
+        if (nv == kRegMaxDepth) {   // only reachable with duplicate columns inside a B row (invalid input)
+            V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+            --nv;
+        }
+        V[nv++] = vals[p];
+        prev_l = l;
+    }
+    while (nv > 1) {
+        V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+        --nv;
+    }
+    return V[0];
+}
+
+template <class P, int TPR, int E>
+__global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
+    using Cf = RegCfg<TPR, E>;
+    using In = typename P::In;
+    using T = typename P::T;
+    using Out = typename P::Out;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int rho = lane / TPR, t = lane % TPR, rowbase = rho * TPR;
+    unsigned char *wb = smem + (size_t)wid * perm_warp_bytes<E, P>();
+    unsigned char *desc = wb + (size_t)rho * Cf::DESC;
+    In *d_a = reinterpret_cast<In *>(desc);
+    int32_t *d_q0 = reinterpret_cast<int32_t *>(desc + 8 * Cf::LCAP);
+    int32_t *d_off = reinterpret_cast<int32_t *>(desc + 12 * Cf::LCAP);
+    T *vals = reinterpret_cast<T *>(wb + reg_stage_bytes(E)) + rho * Cf::CAP;
+    int32_t *cols = reinterpret_cast<int32_t *>(wb + reg_stage_bytes(E) + sizeof(T) * 32 * E) + rho * Cf::CAP;
+    uint8_t *lidx = reinterpret_cast<uint8_t *>(wb + reg_stage_bytes(E) + (sizeof(T) + 4) * 32 * E) + rho * Cf::CAP;
+    const uint64_t keep = l2_keep_policy();
+    const int stride = gridDim.x * nwarps * Cf::RPW;
+
+    for (int r0 = (blockIdx.x * nwarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
+        const int slot = r0 + rho;
+        const bool has_row = slot < j.count;
+        const int row = has_row ? j.rows[slot] : 0;
+        RowIn<In> ri{};
+        if (has_row) ri = row_in<In>(j, row);
+        const int L = has_row ? ri.L : 0;
+
+        int carry = 0;
+        for (int c0 = 0; __any_sync(kFull, c0 < L); c0 += TPR) {
+            const int l = c0 + t;
+            int len = 0;
+            if (l < L) {
+                const int k = ri.acol[l];
+                const int q0 = ri.brp[k];
+                len = ri.brp[k + 1] - q0;
+                d_q0[l] = q0;
+                d_a[l] = ri.aval[l];
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < TPR; d <<= 1) {
+                const int u = __shfl_up_sync(kFull, incl, d, TPR);
+                if (t >= d) incl += u;
+            }
+            if (l < L) d_off[l + 1] = carry + incl;
+            carry += __shfl_sync(kFull, incl, TPR - 1, TPR);
+        }
+        if (t == 0) d_off[0] = 0;
+        const int N = carry;
+        __syncwarp();
+
+        // multiplying phase in list order: position p = i * TPR + t
+        {
+            int l = 0;
+#pragma unroll
+            for (int i0 = 0; i0 < E; i0 += kRegU) {
+                if (!__any_sync(kFull, i0 * TPR < N)) break;
+                int q[kRegU];
+                In a[kRegU];
+#pragma unroll
+                for (int u = 0; u < kRegU; ++u) {
+                    const int p = (i0 + u) * TPR + t;
+                    q[u] = -1;
+                    a[u] = In();
+                    if (p < N) {
+                        while (d_off[l + 1] <= p) ++l;
+                        q[u] = d_q0[l] + (p - d_off[l]);
+                        a[u] = d_a[l];
+                        lidx[p] = (uint8_t)l;
+                    }
+                }
+                int32_t c[kRegU];
+                In v[kRegU];
+#pragma unroll
+                for (int u = 0; u < kRegU; ++u) {
+                    c[u] = 0;
+                    v[u] = In();
+                    if (q[u] >= 0) {
+                        c[u] = ld_keep(ri.bcol + q[u], keep);
+                        v[u] = ld_keep(ri.bval + q[u], keep);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRegU; ++u) {
+                    const int p = (i0 + u) * TPR + t;
+                    if (q[u] >= 0) {
+                        cols[p] = c[u];
+                        vals[p] = P::mul(a[u], v[u]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+
+        // accumulating phase in the recorded order
+        const uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
+        const int64_t obase = has_row ? j.out_rp[row] : 0;
+        const int cap = has_row ? (int)(j.out_rp[row + 1] - obase) : 0;
+        int32_t *ocol = j.out_col + obase;
+        Out *oval = static_cast<Out *>(j.out_val) + obase;
+        const unsigned gmask = (TPR == 32) ? kFull : (((1u << TPR) - 1u) << rowbase);
+        const unsigned lt = (1u << lane) - 1u;
+        int count = 0;
+        for (int jj = 0; __any_sync(kFull, jj * TPR < N); ++jj) {
+            const int pos = jj * TPR + t;
+            uint32_t pe = 0;
+            if (pos < N) pe = pr[pos];
+            const bool start = (pe & kPermStart) != 0;
+            const unsigned msk = __ballot_sync(kFull, start) & gmask;
+            if (start) {
+                const int w = count + __popc(msk & lt);
+                const int p0 = (int)(pe & kPermPos);
+                T v;
+                if (!(pe & kPermMulti)) v = vals[p0];
+                else v = perm_tree_reduce<P>(pr, pos, N, vals, lidx);
+                if (w < cap) {
+                    __stcs(ocol + w, cols[p0]);
+                    __stcs(oval + w, P::fin(v));
+                }
+            }
+            count += __popc(msk);
+        }
+        if (has_row) {
+            if (t == 0 && (count > cap || (j.exact && count != cap))) atomicOr(j.err, 1u);
+            if (t == 0 && j.out_cnt != nullptr) j.out_cnt[row] = count;
+        }
+        __syncwarp();   // descriptors and parked products are reused by the next rows
+    }
+}
+
+template <class P, int TPR, int E>
+cudaError_t launch_perm_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
+    const size_t sm = (size_t)warps * perm_warp_bytes<E, P>();
+    auto kern = k_rows_perm<P, TPR, E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm);
+    if (e != cudaSuccess) return e;
+    const int rows_per_block = warps * RegCfg<TPR, E>::RPW;
+    const int need = (j.count + rows_per_block - 1) / rows_per_block;
+    const int grid = max(1, min(need, sms * max(occ, 1)));
+    kern<<<grid, warps * 32, sm, st>>>(j);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 template <class P, int TPR, int E>
 cudaError_t launch_reg_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
-    if constexpr (!P::kVal) {
+    if constexpr (!P::kVal && !P::kPerm) {
+        if (j.perm != nullptr) return launch_reg_t<PPerm, TPR, E>(j, st, sms, warps);
         if (j.sym_hash) return launch_sym_hash_t<TPR, E>(j, st, sms, warps);
+    }
+    if constexpr (P::kVal) {
+        if (j.perm != nullptr) return launch_perm_t<P, TPR, E>(j, st, sms, warps);
     }
     const size_t sm = (size_t)warps * reg_warp_bytes<P>(E);
     auto kern = k_rows_reg<P, TPR, E>;

@@ -136,6 +136,11 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (bin == kBinRegTop) {
+        RowJob jt = j;
+        jt.reg_keys = 2 * j.reg_keys;
+        return launch_reg_rows<P>(32, jt, st, sms);
+    }
     if (bin >= kBinReg0 && bin < kBinReg0 + kNumRegBins) return launch_reg_rows<P>(reg_bin_tpr(bin), j, st, sms);
     if (bin == kBinWarp) {
         const size_t sm = kWarpsPerBlock * pair_bytes<P>(kWarpCap, kWarpCap);

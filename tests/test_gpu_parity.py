@@ -101,6 +101,7 @@ def test_bins_small_thresholds():
     for keys in (8, 16, 32):
         for sym_hash in (False, True):
             assert_rows_exact(run(A, B, reg_keys=keys, symbolic_hash=sym_hash), ref)
+        assert_rows_exact(run(A, B, reg_keys=keys, reg_top=False), ref)
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
@@ -262,3 +263,27 @@ def test_rmat_sampled(mode, dtype, comp):
     assert_rows_exact(C, oracle.alg1(A, A, rows, prec=mode), rows)
     want_nnz = oracle.symbolic(A, A)
     assert np.array_equal(np.diff(C.rp.cpu().numpy()), want_nnz)
+
+
+def test_float32_error_report_against_f64_oracle():
+    """The FP32 paths against the FP64 oracle (inputs rounded to float, their
+    exact products summed in double): entrywise within the summation bounds
+    of plain float addition over the merge tree's depth, and of TwoSum; the
+    compensated path is at least as accurate in the median."""
+    A = I.rmat(14, 16, seed=71).astype(np.float32)
+    rows = _sample_rows(A.rows, oracle.row_nprod(A, A), 800, 72)
+    Ap = I.CSR(A.rows, A.cols, A.rp, A.col, A.val.astype(np.float64))
+    ref = oracle.gustavson(Ap, Ap, rows, with_abs=True)
+    u32 = 2.0 ** -24
+    depth = int(np.ceil(np.log2(max(2, np.diff(A.rp.astype(np.int64)).max()))))
+    errs = {}
+    for comp in (False, True):
+        C = run(A, A, "precise", np.float32, comp)
+        rp, col, val = C.rp.cpu().numpy(), C.col.cpu().numpy(), C.val.cpu().numpy().astype(np.float64)
+        from helpers import rows_of
+        crp, c, v = rows_of(rp, col, val, rows)
+        assert np.array_equal(c, ref.col)
+        errs[comp] = np.abs(v - ref.val)
+    assert np.all(errs[False] <= (depth + 1) * u32 * ref.abs * 1.0001)
+    assert np.all(errs[True] <= u32 * np.abs(ref.val) + u32 * ref.abs + 3 * depth * u32 ** 2 * ref.abs)
+    assert np.median(errs[True]) <= np.median(errs[False])

@@ -1,0 +1,51 @@
+"""The multi-rank host logic of bench.py on CPU (gloo, world size 2).
+
+The path shards into independent products, one per rank (weak scaling, no
+collective on the data path); the only collectives are the timing barrier and
+the maximum over ranks of the measured time, which the whole-job value uses.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = 10.0 + 5.0 * rank                       # rank 1 is the slow one
+        ms_max = bench.reduce_max(ms, dist, "cpu")
+        value = bench.job_gflops(1000, world, 4, ms_max)
+        dist.barrier()
+        out[rank] = (ms_max, value, bench.rank_seed(rank))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0
+    assert res[0][1] == res[1][1] == pytest.approx(2 * 2.0 * 1000 * 4 / 15e-3 / 1e9)
+    assert res[0][2] != res[1][2]                     # independent products per rank
+
+
+def test_single_process_needs_no_group():
+    import bench
+    assert bench.reduce_max(3.5, None, "cpu") == 3.5
+    assert bench.job_gflops(10, 1, 1, 1.0) == pytest.approx(2e-5)
