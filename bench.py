@@ -43,9 +43,11 @@ METRIC = "SpGEMM GFLOP/s (2*products/s)"
 UNIT = "GFLOP/s"
 WORKLOAD = "ER n=2^20, 16 nnz/row, C=A*A, FP64, BRMerge-Precise"
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
-# capture of the current kernel source; None until captured for this version.
-NUMERIC_REG_TRAFFIC = None
+# DRAM bytes (read + write) of one launch of the dominant kernel (the numeric
+# register-bin kernel on this workload), from an ncu capture of the current
+# kernel source (dram__bytes_read.sum + dram__bytes_write.sum); set to None
+# whenever that kernel changes until it is captured again.
+NUMERIC_REG_TRAFFIC = 3.899572e9 + 3.183006e9
 
 
 def peaks():
@@ -430,6 +432,21 @@ def run_rmat(args):
                                                "rows": int(len(rows))}}
         del dA
         torch.cuda.empty_cache()
+    # BRMerge-Upper: C_bar of every product (about 251 GB here) does not fit
+    # beside C, so it runs in row chunks
+    dA = brm.to_device(A)
+    try:
+        def upper_step():
+            Cx = brm.brm_spgemm_upper(dA, dA, upper_chunk_bytes=16 << 30)
+            del Cx
+
+        ms = _timed(upper_step, 1, 1)
+        out["f64_upper_chunked"] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9,
+                                    "chunk_bytes": 16 << 30}
+    except brm.BrmError as e:
+        out["f64_upper_chunked"] = {"error": str(e)}
+    del dA
+    torch.cuda.empty_cache()
     out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
     out["speedup_f32_twosum_vs_f64"] = out["f64"]["ms_per_step"] / out["f32_twosum"]["ms_per_step"]
     print(json.dumps(out), flush=True)

@@ -115,6 +115,14 @@ typedef struct {
  *                  the register bins still take a register kernel, with 32
  *                  threads of 2 * reg_keys keys; 0: they take the shared-
  *                  memory kernels;
+ *   reg_perm       1 (default): in BRMerge-Precise (and prepared batches)
+ *                  the symbolic pass of the register bins records every
+ *                  row's merge order (2 bytes per product, temporary) and the
+ *                  numeric pass applies it instead of sorting again; the
+ *                  result is the same; 0: the numeric pass sorts by itself;
+ *   reg_num_half   1 (default): with reg_perm, the numeric pass runs each
+ *                  register row with twice the threads and half the keys of
+ *                  its bin where it can (rows of <= 16 threads, >= 16 keys);
  *   symbolic_hash  register bins count a row's distinct columns in the
  *                  symbolic pass with the numeric pass's sorting network on
  *                  bare columns (0, default) or by hashing into a
@@ -129,6 +137,12 @@ typedef struct {
  *   arena_bytes    budget of the device-memory arena for long rows (0 = the
  *                  library picks 1/8 of free memory, at least enough for the
  *                  longest row).
+ *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
+ *                  sizeof value) bytes) processed at once; a larger product
+ *                  is processed in row chunks of at most this size, each
+ *                  compacted on its own, and C assembled from them (peak
+ *                  about twice C plus one chunk).  0 = the whole C_bar when it
+ *                  can be allocated, else chunks of a quarter of free memory.
  */
 typedef struct {
     int32_t validate;
@@ -140,7 +154,10 @@ typedef struct {
     int32_t reg_warps;
     int32_t symbolic_hash;
     int32_t reg_top;
+    int32_t reg_perm;
+    int32_t reg_num_half;
     size_t arena_bytes;
+    size_t upper_chunk_bytes;
 } brm_options;
 
 void brm_options_default(brm_options *opts);
@@ -184,7 +201,9 @@ int brm_spgemm_precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
  * the numeric BRMerge pass writing each row and its size into C_bar, the
  * prefix sum of the row sizes into C.row_ptr, allocation of C and the copy of
  * C_bar into C.  Same result as brm_spgemm_precise, bit for bit.  C_bar needs
- * total_nprod * (4 + sizeof(value)) bytes; BRM_ERR_OOM if it cannot be had.
+ * total_nprod * (4 + sizeof(value)) bytes; when that is more than
+ * opts->upper_chunk_bytes (or cannot be allocated) the rows are processed in
+ * chunks (see brm_options).
  * Synchronises the stream three times (bins, nnz(C), final check), once more
  * with long rows.
  */

@@ -52,7 +52,9 @@ class brm_options(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("compensated", ctypes.c_int32),
                 ("warp_max_nprod", ctypes.c_int32), ("block_max_nprod", ctypes.c_int32),
                 ("reg_max_nprod", ctypes.c_int32), ("reg_keys", ctypes.c_int32), ("reg_warps", ctypes.c_int32),
-                ("symbolic_hash", ctypes.c_int32), ("reg_top", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t)]
+                ("symbolic_hash", ctypes.c_int32), ("reg_top", ctypes.c_int32), ("reg_perm", ctypes.c_int32),
+                ("reg_num_half", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
+                ("upper_chunk_bytes", ctypes.c_size_t)]
 
 
 class BrmError(RuntimeError):
@@ -242,7 +244,8 @@ def _stream(stream=None):
 
 
 def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
-            reg_keys=0, reg_warps=0, symbolic_hash=False, reg_top=True, arena_bytes=0) -> brm_options:
+            reg_keys=0, reg_warps=0, symbolic_hash=False, reg_top=True, reg_perm=True, reg_num_half=True,
+            arena_bytes=0, upper_chunk_bytes=0) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -259,7 +262,10 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
         o.reg_warps = reg_warps
     o.symbolic_hash = int(bool(symbolic_hash))
     o.reg_top = int(bool(reg_top))
+    o.reg_perm = int(bool(reg_perm))
+    o.reg_num_half = int(bool(reg_num_half))
     o.arena_bytes = arena_bytes
+    o.upper_chunk_bytes = upper_chunk_bytes
     return o
 
 

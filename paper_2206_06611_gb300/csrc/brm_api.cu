@@ -207,6 +207,8 @@ brm_options resolve(const brm_options *o) {
     if (r.reg_warps < 1 || r.reg_warps > 8) r.reg_warps = kRegWarpsDefault;
     if (r.reg_max_nprod == 0 || r.reg_max_nprod > r.reg_keys * kRegMaxTpr) r.reg_max_nprod = r.reg_keys * kRegMaxTpr;
     r.reg_top = r.reg_top != 0 ? 1 : 0;
+    r.reg_perm = r.reg_perm != 0 ? 1 : 0;
+    r.reg_num_half = r.reg_num_half != 0 ? 1 : 0;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -230,6 +232,8 @@ int reg_top_ok(const brm_options &o, int64_t bcols) {
 // Result of the binning step.
 struct Plan {
     BinStats stats{};
+    uint8_t *bin_of = nullptr;          // device: the bin of every row
+    int64_t *nprod = nullptr;           // device: nprod_i of every row
     int32_t *rows = nullptr;            // device: the rows of every bin, bin after bin
     int64_t base[kNumBins] = {};        // where bin b starts in rows
     int64_t *long_nprod = nullptr;      // device, per long slot (binning order)
@@ -271,6 +275,8 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
     if ((rc = get(mem, bin_of, m1, "row bins"))) return rc;
     if ((rc = get(mem, pl.rows, m1, "bin row lists"))) return rc;
     if (!nprod && (rc = get(mem, nprod, m1, "row nprod"))) return rc;
+    pl.bin_of = bin_of;
+    pl.nprod = nprod;
     BinArgs a{};
     a.m = m;
     a.arp = src.arp;
@@ -445,6 +451,7 @@ RowJob base_job(const Src &src, const brm_options &o) {
     j.reg_keys = o.reg_keys;
     j.reg_warps = o.reg_warps;
     j.sym_hash = o.symbolic_hash ? 1 : 0;
+    j.num_half = o.reg_num_half ? 1 : 0;
     j.arp = src.arp;
     j.acol = src.acol;
     j.aval = src.aval;
@@ -462,17 +469,43 @@ VKind value_kind(int32_t dtype, const brm_options &o) {
 size_t value_bytes(int32_t dtype) { return dtype == BRM_F64 ? 8 : 4; }
 
 // Symbolic phase into row_ptr (m+1, device); returns nnz(C) on the host.
-int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *row_ptr, int64_t *nnz) {
+// The recorded orders of the register-bin rows (written by the symbolic
+// pass, read by the numeric pass): one 16-bit entry per product, row i's
+// entries at perm_off[i].
+struct PermBuf {
+    uint16_t *perm = nullptr;
+    int64_t *perm_off = nullptr;
+};
+
+int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *row_ptr, int64_t *nnz,
+                  PermBuf *pb = nullptr) {
     const int64_t m = src.m;
     int64_t *row_nnz;
     int rc = get(mem, row_nnz, (size_t)std::max<int64_t>(m, 1), "row counts");
     if (rc) return rc;
     if ((rc = make_plan(mem, src, o, pl, nullptr, row_nnz))) return rc;
-    RowJob j = base_job(src, o);
-    j.out_cnt = row_nnz;
-    if ((rc = run_pass(mem, kIdx, pl, o, j))) return rc;
     void *tmp;
     if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
+    RowJob j = base_job(src, o);
+    j.out_cnt = row_nnz;
+    if (pb && o.reg_perm && !o.symbolic_hash && pl.stats.reg_nprod > 0) {
+        int64_t *masked;
+        if ((rc = get(mem, masked, (size_t)std::max<int64_t>(m, 1), "register-row products"))) return rc;
+        if ((rc = get(mem, pb->perm_off, (size_t)m + 1, "recorded-order offsets"))) return rc;
+        size_t reg_rows = 0;
+        for (int b = kBinReg0; b < kBinReg0 + kNumRegBins; ++b) reg_rows += (size_t)pl.stats.count[b];
+        // every row's segment padded to a multiple of 16 entries
+        if ((rc = get(mem, pb->perm, (size_t)pl.stats.reg_nprod + 15 * reg_rows, "recorded orders"))) return rc;
+        {
+            PhaseScope ps(kPhScan, mem.st);
+            BRM_CUDA(launch_reg_nprod(m, pl.bin_of, pl.nprod, masked, mem.st));
+            BRM_CUDA(launch_scan(masked, pb->perm_off, m, tmp, mem.st));
+        }
+        mem.free_one(masked);
+        j.perm = pb->perm;
+        j.perm_off = pb->perm_off;
+    }
+    if ((rc = run_pass(mem, kIdx, pl, o, j))) return rc;
     {
         PhaseScope ps(kPhScan, mem.st);
         BRM_CUDA(launch_scan(row_nnz, row_ptr, m, tmp, mem.st));
@@ -499,7 +532,8 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     Plan pl;
     int64_t nnz = 0;
     const Src src = src_of(A, B);
-    if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz))) return rc;
+    PermBuf pb;
+    if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz, &pb))) return rc;
     int32_t *col;
     if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
     void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
@@ -508,12 +542,130 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     j.out_rp = rp;
     j.out_col = col;
     j.out_val = val;
+    j.perm = pb.perm;
+    j.perm_off = pb.perm_off;
     unsigned int *err;
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
     j.exact = 1;
     if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
+    if ((rc = check_flag(mem, err))) return rc;
+    mem.detach(rp);
+    mem.detach(col);
+    mem.detach(val);
+    C->rows = m;
+    C->cols = B->cols;
+    C->nnz = nnz;
+    C->row_ptr = rp;
+    C->col_idx = col;
+    C->val = val;
+    C->dtype = A->dtype;
+    return BRM_OK;
+}
+
+// BRMerge-Upper in row chunks whose C_bar fits `budget` bytes (the paper's
+// Upper allocates C_bar in per-thread parts, Section III-D-1; here the parts
+// are processed one after another so that C_bar never exceeds the budget).
+// Every chunk is merged into the reused C_bar and compacted into a buffer of
+// its exact size; C is then allocated and the chunks copied into it in order.
+// Peak memory: about twice C plus one chunk's C_bar.
+int upper_chunked(Mem &mem, const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options &o,
+                  const Src &src, int64_t *nprod, int64_t *row_size, const int64_t *cbar_off, void *tmp,
+                  size_t budget) {
+    const int64_t m = A->rows;
+    const size_t vb = value_bytes(A->dtype), per = 4 + vb;
+    std::vector<int64_t> off_h((size_t)m + 1);
+    BRM_CUDA(cudaMemcpyAsync(off_h.data(), cbar_off, ((size_t)m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));
+    const int64_t cap = std::max<int64_t>((int64_t)(budget / per), 1);
+    std::vector<int64_t> bounds{0};
+    int64_t biggest = 1;
+    while (bounds.back() < m) {
+        const int64_t r0 = bounds.back();
+        // the most rows from r0 whose products fit the chunk (at least one row)
+        int64_t r1 = (int64_t)(std::upper_bound(off_h.begin() + r0 + 1, off_h.end(), off_h[r0] + cap) -
+                               off_h.begin()) - 1;
+        r1 = std::max(r1, r0 + 1);
+        biggest = std::max(biggest, off_h[r1] - off_h[r0]);
+        bounds.push_back(r1);
+    }
+    int32_t *ccol;
+    int rc = get(mem, ccol, (size_t)biggest, "C_bar chunk columns");
+    if (rc) return rc;
+    void *cval = mem.get((size_t)biggest * vb);
+    if (!cval) return fail(BRM_ERR_OOM, "allocation of a C_bar chunk (%lld products) failed", (long long)biggest);
+    int64_t maxrows = 1;
+    for (size_t c = 0; c + 1 < bounds.size(); ++c) maxrows = std::max(maxrows, bounds[c + 1] - bounds[c]);
+    int64_t *loc_off, *loc_rp;
+    if ((rc = get(mem, loc_off, (size_t)maxrows + 1, "chunk C_bar offsets"))) return rc;
+    if ((rc = get(mem, loc_rp, (size_t)maxrows + 1, "chunk row pointer"))) return rc;
+    unsigned int *err;
+    if ((rc = get(mem, err, 1, "error flag"))) return rc;
+    BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
+    struct Piece { int32_t *col; void *val; int64_t nnz; };
+    std::vector<Piece> pieces;
+    const VKind v = value_kind(A->dtype, o);
+    for (size_t c = 0; c + 1 < bounds.size(); ++c) {
+        const int64_t r0 = bounds[c], rows = bounds[c + 1] - bounds[c];
+        Src sub = src;
+        sub.m = rows;
+        sub.arp = A->row_ptr + r0;
+        Plan pc;
+        if ((rc = make_plan(mem, sub, o, pc, nprod + r0, row_size + r0))) return rc;
+        {
+            PhaseScope ps(kPhScan, mem.st);
+            BRM_CUDA(launch_scan(nprod + r0, loc_off, rows, tmp, mem.st));
+        }
+        RowJob j = base_job(sub, o);
+        j.out_rp = loc_off;
+        j.out_col = ccol;
+        j.out_val = cval;
+        j.out_cnt = row_size + r0;
+        j.err = err;
+        if ((rc = run_pass(mem, v, pc, o, j))) return rc;
+        {
+            PhaseScope ps(kPhScan, mem.st);
+            BRM_CUDA(launch_scan(row_size + r0, loc_rp, rows, tmp, mem.st));
+        }
+        Piece pc_out{nullptr, nullptr, 0};
+        BRM_CUDA(cudaMemcpyAsync(&pc_out.nnz, loc_rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
+        BRM_CUDA(cudaStreamSynchronize(mem.st));
+        if ((rc = get(mem, pc_out.col, (size_t)std::max<int64_t>(pc_out.nnz, 1), "chunk columns"))) return rc;
+        pc_out.val = mem.get((size_t)std::max<int64_t>(pc_out.nnz, 1) * vb);
+        if (!pc_out.val) return fail(BRM_ERR_OOM, "allocation of a compacted chunk failed");
+        {
+            PhaseScope ps(kPhCompact, mem.st);
+            BRM_CUDA(launch_compact(rows, loc_off, loc_rp, ccol, cval, pc_out.col, pc_out.val, vb, mem.st));
+        }
+        pieces.push_back(pc_out);
+    }
+    mem.free_one(cval);
+    mem.free_one(ccol);
+    int64_t *rp;
+    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    {
+        PhaseScope ps(kPhScan, mem.st);
+        BRM_CUDA(launch_scan(row_size, rp, m, tmp, mem.st));
+    }
+    int64_t nnz = 0;
+    for (const Piece &p : pieces) nnz += p.nnz;
+    int32_t *col;
+    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * vb);
+    if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
+    int64_t at = 0;
+    for (const Piece &p : pieces) {
+        if (p.nnz > 0) {
+            BRM_CUDA(cudaMemcpyAsync(col + at, p.col, (size_t)p.nnz * 4, cudaMemcpyDeviceToDevice, mem.st));
+            BRM_CUDA(cudaMemcpyAsync(static_cast<char *>(val) + (size_t)at * vb, p.val, (size_t)p.nnz * vb,
+                                     cudaMemcpyDeviceToDevice, mem.st));
+        }
+        at += p.nnz;
+        mem.free_one(p.col);
+        mem.free_one(p.val);
+    }
     if ((rc = check_flag(mem, err))) return rc;
     mem.detach(rp);
     mem.detach(col);
@@ -554,10 +706,24 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
         BRM_CUDA(launch_scan(nprod, cbar_off, m, tmp, mem.st));
     }
     const int64_t total = (int64_t)pl.stats.total_nprod;
-    int32_t *ccol;
-    if ((rc = get(mem, ccol, (size_t)std::max<int64_t>(total, 1), "C_bar columns"))) return rc;
-    void *cval = mem.get((size_t)std::max<int64_t>(total, 1) * vb);
-    if (!cval) return fail(BRM_ERR_OOM, "allocation of C_bar values (%lld products) failed", (long long)total);
+    const size_t per = 4 + vb;
+    size_t budget = o.upper_chunk_bytes;
+    int32_t *ccol = nullptr;
+    void *cval = nullptr;
+    if (budget == 0 || (size_t)std::max<int64_t>(total, 1) * per <= budget) {
+        ccol = static_cast<int32_t *>(mem.get((size_t)std::max<int64_t>(total, 1) * 4));
+        if (ccol) cval = mem.get((size_t)std::max<int64_t>(total, 1) * vb);
+        if (!ccol || !cval) {
+            // the whole C_bar does not fit: row chunks of a quarter of what is free
+            mem.free_one(ccol);
+            ccol = nullptr;
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = (size_t)4 << 30; }
+            budget = std::max<size_t>(fr / 4, (size_t)1 << 20);
+        }
+    }
+    if (!cval)
+        return upper_chunked(mem, A, B, C, o, src, nprod, row_size, cbar_off, tmp, budget);
     // step 4: BRMerge into C_bar, recording the row sizes
     RowJob j = base_job(src, o);
     j.out_rp = cbar_off;
@@ -671,6 +837,7 @@ struct brm_batch {
     brm::Plan pl;
     brm::LongPlan lp;
     brm::RowJob job{};
+    brm::PermBuf pb;
     brm::VKind v = brm::kF64;
     int32_t count = 0;
     int64_t nnz = 0;
@@ -710,7 +877,7 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     int rc = batch_setup(b->mem, count, A, B, b->o, b->src, b->row0);
     const int64_t M = b->src.m;
     if (!rc) rc = get(b->mem, b->rp, (size_t)M + 1, "C.row_ptr");
-    if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz);
+    if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz, &b->pb);
     if (!rc) rc = get(b->mem, b->col, (size_t)std::max<int64_t>(b->nnz, 1), "C.col_idx");
     if (!rc) {
         b->val = b->mem.get((size_t)std::max<int64_t>(b->nnz, 1) * value_bytes(b->src.dtype));
@@ -729,6 +896,8 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     j.out_val = b->val;
     j.err = b->err;
     j.exact = 1;
+    j.perm = b->pb.perm;
+    j.perm_off = b->pb.perm_off;
     b->job = j;
     *out = b;
     return BRM_OK;
@@ -810,6 +979,8 @@ void brm_options_default(brm_options *o) {
     o->reg_keys = kRegKeysDefault;
     o->reg_warps = kRegWarpsDefault;
     o->reg_top = 1;
+    o->reg_perm = 1;
+    o->reg_num_half = 1;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
 }

@@ -88,7 +88,9 @@ __global__ void k_reg_nprod(int64_t m, const uint8_t *bin_of, const int64_t *npr
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) {
         const int b = bin_of[i];
-        out[i] = (b >= kBinReg0 && b < kBinReg0 + kNumRegBins) ? nprod[i] : 0;
+        // a row's recorded order is padded to a multiple of 16 entries (one
+        // 32-byte sector), so that every sector is written whole
+        out[i] = (b >= kBinReg0 && b < kBinReg0 + kNumRegBins) ? ((nprod[i] + 15) & ~int64_t(15)) : 0;
     }
 }
 

@@ -192,6 +192,7 @@ struct RowJob {
     // applied by the numeric pass); null: the numeric pass sorts by itself
     uint16_t *perm;
     const int64_t *perm_off;    // per row: where its order starts in perm
+    int32_t num_half;           // numeric from a recorded order: half the keys, twice the threads
     // long rows only: per slot, the arena offset (bytes) and the product count
     char *arena;
     const int64_t *arena_off;

@@ -102,7 +102,8 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t st);
 cudaError_t launch_fill_prod_of(const ProdDesc *prods, const int64_t *rows_of, int32_t count, int32_t *prod_of,
                                 cudaStream_t st);
 cudaError_t launch_bin_scatter(const BinArgs &a, cudaStream_t st);
-// out[i] = nprod[i] if row i is in a register bin, else 0
+// out[i] = nprod[i] rounded up to a multiple of 16 if row i is in a register
+// bin, else 0
 cudaError_t launch_reg_nprod(int64_t m, const uint8_t *bin_of, const int64_t *nprod, int64_t *out, cudaStream_t st);
 cudaError_t launch_validate(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rp, const int32_t *col,
                             BinStats *st, cudaStream_t stream);

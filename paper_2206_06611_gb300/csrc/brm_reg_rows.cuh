@@ -298,25 +298,37 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
         reg_bitonic_sort<TPR, E>(key, t);
 
         if constexpr (P::kPerm) {
-            // symbolic, recording the order: every sorted position gets its
-            // product's position and the run marks; the runs are counted
-            __syncwarp();   // every lane is done with the descriptors (same memory)
-#pragma unroll
-            for (int i = 0; i < E; ++i) stage[i * 33 + lane] = key[i];
-            __syncwarp();
-            uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
+            // symbolic, recording the order: thread t holds sorted positions
+            // E t .. E t + E - 1; every entry gets its product's position and
+            // the run marks (neighbours across threads by shuffles), and the
+            // thread stores its E entries with 16-byte streaming stores (a
+            // row's segment is padded to a multiple of 16 entries), which
+            // keep B's columns in L2
+            const uint32_t before = __shfl_up_sync(kFull, key[E - 1], 1, TPR);
+            const uint32_t after = __shfl_down_sync(kFull, key[0], 1, TPR);
+            uint32_t packed[E / 2];
             int cnt = 0;
-            for (int jj = 0; __any_sync(kFull, jj * TPR < N); ++jj) {
-                const int pos = jj * TPR + t;
-                if (pos < N) {
-                    const uint32_t kk = reg_sorted_key<E>(stage, rowbase, pos);
-                    const uint32_t c = kk >> SB;
-                    const bool start = pos == 0 || (reg_sorted_key<E>(stage, rowbase, pos - 1) >> SB) != c;
-                    const bool multi =
-                        start && pos + 1 < N && (reg_sorted_key<E>(stage, rowbase, pos + 1) >> SB) == c;
-                    pr[pos] = (uint16_t)((kk & SMASK) | (start ? kPermStart : 0u) | (multi ? kPermMulti : 0u));
-                    cnt += start ? 1 : 0;
-                }
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const uint32_t c = key[i] >> SB;
+                const uint32_t prv = (i == 0) ? before : key[i - 1];
+                const uint32_t nxt = (i + 1 < E) ? key[i + 1] : ((t + 1 < TPR) ? after : kKeyPad);
+                const bool real = key[i] != kKeyPad;
+                const bool start = real && ((i == 0 && t == 0) || (prv >> SB) != c);
+                const bool multi = start && nxt != kKeyPad && (nxt >> SB) == c;
+                const uint32_t e = real ? ((key[i] & SMASK) | (start ? kPermStart : 0u) | (multi ? kPermMulti : 0u))
+                                        : 0u;
+                if (i & 1) packed[i >> 1] |= e << 16; else packed[i >> 1] = e;
+                cnt += start ? 1 : 0;
+            }
+            if (has_row) {
+                const int npad = (N + 15) & ~15;
+                uint4 *dst = reinterpret_cast<uint4 *>(j.perm + j.perm_off[row] + E * t);
+#pragma unroll
+                for (int h = 0; h < E / 8; ++h)
+                    if (E * t + 8 * h < npad)
+                        __stcs(dst + h, make_uint4(packed[4 * h], packed[4 * h + 1], packed[4 * h + 2],
+                                                   packed[4 * h + 3]));
             }
 #pragma unroll
             for (int d = 1; d < TPR; d <<= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
@@ -507,9 +519,27 @@ __host__ __device__ constexpr size_t perm_warp_bytes() {
     return reg_stage_bytes(E) + (sizeof(typename P::T) + sizeof(int32_t) + sizeof(uint8_t)) * 32 * (size_t)E;
 }
 
+// Asynchronous 4- and 8-byte copies global -> shared (cp.async), loaded under
+// the L2 evict-last policy like the other gathers of B.
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src, uint64_t pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src, uint64_t pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "l"(pol)
+                 : "memory");
+}
+template <class In>
+__device__ __forceinline__ void cp_async_val(In *dst, const In *src, uint64_t pol) {
+    if constexpr (sizeof(In) == 8) cp_async_8(dst, src, pol); else cp_async_4(dst, src, pol);
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class P>
-__device__ __noinline__ typename P::T perm_tree_reduce(const uint16_t *pr, int P0, int N, const typename P::T *vals,
-                                                       const uint8_t *lidx) {
+__device__ __noinline__ typename P::T perm_tree_reduce(const uint16_t *pr, int P0, int N,
+                                                       const typename P::T *vals, const uint8_t *lidx) {
     using T = typename P::T;
     T V[kRegMaxDepth];
     int G[kRegMaxDepth];
@@ -556,6 +586,7 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
     In *d_a = reinterpret_cast<In *>(desc);
     int32_t *d_q0 = reinterpret_cast<int32_t *>(desc + 8 * Cf::LCAP);
     int32_t *d_off = reinterpret_cast<int32_t *>(desc + 12 * Cf::LCAP);
+    // one slot per product: the copied B value, then (in place) the product
     T *vals = reinterpret_cast<T *>(wb + reg_stage_bytes(E)) + rho * Cf::CAP;
     int32_t *cols = reinterpret_cast<int32_t *>(wb + reg_stage_bytes(E) + sizeof(T) * 32 * E) + rho * Cf::CAP;
     uint8_t *lidx = reinterpret_cast<uint8_t *>(wb + reg_stage_bytes(E) + (sizeof(T) + 4) * 32 * E) + rho * Cf::CAP;
@@ -569,6 +600,7 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
         RowIn<In> ri{};
         if (has_row) ri = row_in<In>(j, row);
         const int L = has_row ? ri.L : 0;
+        const uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
 
         int carry = 0;
         for (int c0 = 0; __any_sync(kFull, c0 < L); c0 += TPR) {
@@ -592,53 +624,45 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
         }
         if (t == 0) d_off[0] = 0;
         const int N = carry;
+        // this thread's recorded entries (output positions jj * TPR + t),
+        // in flight while the products are gathered
+        uint16_t pe[E];
+#pragma unroll
+        for (int jj = 0; jj < E; ++jj) {
+            const int pos = jj * TPR + t;
+            pe[jj] = pos < N ? __ldcs(pr + pos) : (uint16_t)0;
+        }
         __syncwarp();
 
-        // multiplying phase in list order: position p = i * TPR + t
+        // multiplying phase: every product's column and B value copied
+        // asynchronously to its position p = i * TPR + t (list order)
         {
             int l = 0;
+            uint8_t li[E];
 #pragma unroll
-            for (int i0 = 0; i0 < E; i0 += kRegU) {
-                if (!__any_sync(kFull, i0 * TPR < N)) break;
-                int q[kRegU];
-                In a[kRegU];
-#pragma unroll
-                for (int u = 0; u < kRegU; ++u) {
-                    const int p = (i0 + u) * TPR + t;
-                    q[u] = -1;
-                    a[u] = In();
-                    if (p < N) {
-                        while (d_off[l + 1] <= p) ++l;
-                        q[u] = d_q0[l] + (p - d_off[l]);
-                        a[u] = d_a[l];
-                        lidx[p] = (uint8_t)l;
-                    }
+            for (int i = 0; i < E; ++i) {
+                const int p = i * TPR + t;
+                li[i] = 0;
+                if (p < N) {
+                    while (d_off[l + 1] <= p) ++l;
+                    const int q = d_q0[l] + (p - d_off[l]);
+                    li[i] = (uint8_t)l;
+                    lidx[p] = (uint8_t)l;
+                    cp_async_4(cols + p, ri.bcol + q, keep);
+                    cp_async_val(reinterpret_cast<In *>(vals + p), ri.bval + q, keep);
                 }
-                int32_t c[kRegU];
-                In v[kRegU];
+            }
+            cp_async_wait_all();
+            // the products, each rounded, in place of the copied B values
 #pragma unroll
-                for (int u = 0; u < kRegU; ++u) {
-                    c[u] = 0;
-                    v[u] = In();
-                    if (q[u] >= 0) {
-                        c[u] = ld_keep(ri.bcol + q[u], keep);
-                        v[u] = ld_keep(ri.bval + q[u], keep);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kRegU; ++u) {
-                    const int p = (i0 + u) * TPR + t;
-                    if (q[u] >= 0) {
-                        cols[p] = c[u];
-                        vals[p] = P::mul(a[u], v[u]);
-                    }
-                }
+            for (int i = 0; i < E; ++i) {
+                const int p = i * TPR + t;
+                if (p < N) vals[p] = P::mul(d_a[li[i]], *reinterpret_cast<const In *>(vals + p));
             }
         }
         __syncwarp();
 
         // accumulating phase in the recorded order
-        const uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
         const int64_t obase = has_row ? j.out_rp[row] : 0;
         const int cap = has_row ? (int)(j.out_rp[row + 1] - obase) : 0;
         int32_t *ocol = j.out_col + obase;
@@ -646,18 +670,18 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
         const unsigned gmask = (TPR == 32) ? kFull : (((1u << TPR) - 1u) << rowbase);
         const unsigned lt = (1u << lane) - 1u;
         int count = 0;
-        for (int jj = 0; __any_sync(kFull, jj * TPR < N); ++jj) {
-            const int pos = jj * TPR + t;
-            uint32_t pe = 0;
-            if (pos < N) pe = pr[pos];
-            const bool start = (pe & kPermStart) != 0;
+#pragma unroll
+        for (int jj = 0; jj < E; ++jj) {
+            if (!__any_sync(kFull, jj * TPR < N)) break;
+            const uint32_t e = pe[jj];
+            const bool start = (e & kPermStart) != 0;
             const unsigned msk = __ballot_sync(kFull, start) & gmask;
             if (start) {
                 const int w = count + __popc(msk & lt);
-                const int p0 = (int)(pe & kPermPos);
+                const int p0 = (int)(e & kPermPos);
                 T v;
-                if (!(pe & kPermMulti)) v = vals[p0];
-                else v = perm_tree_reduce<P>(pr, pos, N, vals, lidx);
+                if (!(e & kPermMulti)) v = vals[p0];
+                else v = perm_tree_reduce<P>(pr, jj * TPR + t, N, vals, lidx);
                 if (w < cap) {
                     __stcs(ocol + w, cols[p0]);
                     __stcs(oval + w, P::fin(v));
@@ -669,7 +693,7 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
             if (t == 0 && (count > cap || (j.exact && count != cap))) atomicOr(j.err, 1u);
             if (t == 0 && j.out_cnt != nullptr) j.out_cnt[row] = count;
         }
-        __syncwarp();   // descriptors and parked products are reused by the next rows
+        __syncwarp();   // descriptors and copied products are reused by the next rows
     }
 }
 
@@ -697,7 +721,13 @@ cudaError_t launch_reg_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
         if (j.sym_hash) return launch_sym_hash_t<TPR, E>(j, st, sms, warps);
     }
     if constexpr (P::kVal) {
-        if (j.perm != nullptr) return launch_perm_t<P, TPR, E>(j, st, sms, warps);
+        if (j.perm != nullptr) {
+            // the same rows with twice the threads of half the keys (same
+            // products and lists per row): more warps in flight for the gathers
+            if constexpr (TPR <= 16 && E >= 16)
+                if (j.num_half) return launch_perm_t<P, 2 * TPR, E / 2>(j, st, sms, warps);
+            return launch_perm_t<P, TPR, E>(j, st, sms, warps);
+        }
     }
     const size_t sm = (size_t)warps * reg_warp_bytes<P>(E);
     auto kern = k_rows_reg<P, TPR, E>;

@@ -102,6 +102,8 @@ def test_bins_small_thresholds():
         for sym_hash in (False, True):
             assert_rows_exact(run(A, B, reg_keys=keys, symbolic_hash=sym_hash), ref)
         assert_rows_exact(run(A, B, reg_keys=keys, reg_top=False), ref)
+        assert_rows_exact(run(A, B, reg_keys=keys, reg_perm=False), ref)
+        assert_rows_exact(run(A, B, reg_keys=keys, reg_num_half=False), ref)
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
@@ -126,6 +128,7 @@ def test_register_bins_every_size(mode, dtype, comp):
         ref = oracle.alg1(A, Bm, prec=mode)
         for keys in (8, 16, 32):
             assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys), ref)
+            assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys, reg_perm=False), ref)
             assert_rows_exact(run(A, Bm, "upper", dtype, comp, reg_keys=keys), ref)
 
 
@@ -137,6 +140,17 @@ def test_register_bins_wide_B():
     for L, seed in ((100, 37), (40, 38), (3, 39)):   # block bin, register bins of 8 and 1 threads
         X = I.erdos_renyi(300, L, seed=seed, ncols=k)
         assert_rows_exact(run(X, B), oracle.alg1(X, B))
+
+
+@pytest.mark.parametrize("chunk", [1, 4096, 200000])
+def test_upper_in_row_chunks(chunk):
+    """BRMerge-Upper with a C_bar budget smaller than the product: row chunks
+    (down to one row each) give the same C as BRMerge-Precise."""
+    A, B = bins_matrix(seed=9)
+    ref = oracle.alg1(A, B)
+    Cu = run(A, B, "upper", upper_chunk_bytes=chunk)
+    assert_rows_exact(Cu, ref)
+    same(Cu, run(A, B, "precise"))
 
 
 def test_long_rows_small_arena_batches():
