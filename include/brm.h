@@ -260,8 +260,9 @@ int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t
  *   dC           device values of G on C's pattern (A's dtype).
  *   dA_val       device, A.nnz values, written (NULL: not computed).
  *   dB_val       device, B.nnz values, overwritten (NULL: not computed).
- * dA is summed sequentially per entry (deterministic); dB is accumulated with
- * atomic additions, so its rounding may differ between runs.  Returns
+ * One GPU thread per stored entry of A.  dA is summed sequentially per entry
+ * (deterministic); dB is accumulated with atomic additions, so its rounding
+ * may differ between runs.  Returns
  * BRM_ERR_INVALID if C's pattern misses a column.  Synchronises the stream
  * once.  opts is unused (may be NULL); alloc provides one 4-byte flag.
  */

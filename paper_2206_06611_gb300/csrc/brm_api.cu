@@ -100,15 +100,22 @@ struct PhaseScope {
 
 // Device memory of one call.  Everything still owned at destruction (error
 // paths, workspace) is released; arrays handed to the caller are detached.
+//
+// Workspace of a known size can be reserved up front as one block (reserve):
+// later get() calls are carved from it, so a call makes one allocator call
+// for its workspace instead of one per array.  Arrays handed to the caller
+// always come from get_direct().
 struct Mem {
     const brm_allocator *al;
     cudaStream_t st;
     std::vector<void *> owned;
+    char *slab = nullptr;
+    size_t slab_size = 0, slab_used = 0;
 
     Mem(const brm_allocator *a, cudaStream_t s) : al(a), st(s) {}
     ~Mem() { release_all(); }
 
-    void *get(size_t bytes) {
+    void *get_direct(size_t bytes) {
         if (bytes == 0) bytes = 256;
         void *p = nullptr;
         if (al && al->alloc) {
@@ -120,8 +127,26 @@ struct Mem {
         if (p) owned.push_back(p);
         return p;
     }
+    void reserve(size_t bytes) {
+        if (slab) return;
+        slab = static_cast<char *>(get_direct(bytes));
+        slab_size = slab ? bytes : 0;
+        slab_used = 0;
+    }
+    bool in_slab(const void *p) const {
+        return slab && p >= slab && static_cast<const char *>(p) < slab + slab_size;
+    }
+    void *get(size_t bytes) {
+        const size_t b = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);
+        if (slab && slab_used + b <= slab_size) {
+            void *p = slab + slab_used;
+            slab_used += b;
+            return p;
+        }
+        return get_direct(bytes);
+    }
     void free_one(void *p) {
-        if (!p) return;
+        if (!p || in_slab(p)) return;   // carved workspace goes with the block
         auto it = std::find(owned.begin(), owned.end(), p);
         if (it != owned.end()) owned.erase(it);
         release(p);
@@ -146,6 +171,18 @@ int get(Mem &mem, T *&p, size_t count, const char *what) {
     if (!p) return fail(BRM_ERR_OOM, "allocation of %zu bytes for %s failed", count * sizeof(T), what);
     return BRM_OK;
 }
+
+// An array that is handed to the caller (never carved from the workspace).
+template <class T>
+int get_own(Mem &mem, T *&p, size_t count, const char *what) {
+    p = static_cast<T *>(mem.get_direct(count * sizeof(T)));
+    if (!p) return fail(BRM_ERR_OOM, "allocation of %zu bytes for %s failed", count * sizeof(T), what);
+    return BRM_OK;
+}
+
+// Workspace bytes that a Precise / symbolic / Upper call over m rows needs
+// before its first synchronisation (bins, counts, scans, offsets).
+size_t row_workspace_bytes(int64_t m);
 
 int check_csr(const brm_csr *M, const char *name, bool need_val) {
     if (!M) return fail(BRM_ERR_INVALID, "%s is NULL", name);
@@ -227,6 +264,13 @@ int reg_max_tpr(const brm_options &o, int64_t bcols) {
 int reg_top_ok(const brm_options &o, int64_t bcols) {
     return o.reg_keys < 32 && reg_max_tpr(o, bcols) == kRegMaxTpr && o.reg_max_nprod >= 32 * o.reg_keys &&
            o.reg_top && bcols <= reg_col_limit(32, 2 * o.reg_keys);
+}
+
+size_t row_workspace_bytes(int64_t m) {
+    const size_t m1 = (size_t)std::max<int64_t>(m, 1) + 1;
+    // statistics and flags; per row: bin (1), row list (4), nprod (8), counts
+    // (8), order sizes (8), order offsets (8); two scan workspaces
+    return 8 * 256 + m1 * (1 + 4 + 8 + 8 + 8 + 8) + 2 * scan_tmp_bytes(m) + 8 * 256;
 }
 
 // Result of the binning step.
@@ -528,15 +572,16 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
     const int64_t m = A->rows;
     int64_t *rp;
-    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    if ((rc = get_own(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    mem.reserve(row_workspace_bytes(m));
     Plan pl;
     int64_t nnz = 0;
     const Src src = src_of(A, B);
     PermBuf pb;
     if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz, &pb))) return rc;
     int32_t *col;
-    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
-    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
+    if ((rc = get_own(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get_direct((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
     if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
     RowJob j = base_job(src, o);
     j.out_rp = rp;
@@ -632,8 +677,8 @@ int upper_chunked(Mem &mem, const brm_csr *A, const brm_csr *B, brm_csr_out *C, 
         Piece pc_out{nullptr, nullptr, 0};
         BRM_CUDA(cudaMemcpyAsync(&pc_out.nnz, loc_rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaStreamSynchronize(mem.st));
-        if ((rc = get(mem, pc_out.col, (size_t)std::max<int64_t>(pc_out.nnz, 1), "chunk columns"))) return rc;
-        pc_out.val = mem.get((size_t)std::max<int64_t>(pc_out.nnz, 1) * vb);
+        if ((rc = get_own(mem, pc_out.col, (size_t)std::max<int64_t>(pc_out.nnz, 1), "chunk columns"))) return rc;
+        pc_out.val = mem.get_direct((size_t)std::max<int64_t>(pc_out.nnz, 1) * vb);
         if (!pc_out.val) return fail(BRM_ERR_OOM, "allocation of a compacted chunk failed");
         {
             PhaseScope ps(kPhCompact, mem.st);
@@ -644,7 +689,7 @@ int upper_chunked(Mem &mem, const brm_csr *A, const brm_csr *B, brm_csr_out *C, 
     mem.free_one(cval);
     mem.free_one(ccol);
     int64_t *rp;
-    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    if ((rc = get_own(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
     {
         PhaseScope ps(kPhScan, mem.st);
         BRM_CUDA(launch_scan(row_size, rp, m, tmp, mem.st));
@@ -652,8 +697,8 @@ int upper_chunked(Mem &mem, const brm_csr *A, const brm_csr *B, brm_csr_out *C, 
     int64_t nnz = 0;
     for (const Piece &p : pieces) nnz += p.nnz;
     int32_t *col;
-    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
-    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * vb);
+    if ((rc = get_own(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get_direct((size_t)std::max<int64_t>(nnz, 1) * vb);
     if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
     int64_t at = 0;
     for (const Piece &p : pieces) {
@@ -692,6 +737,7 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     const int64_t m = A->rows;
     const size_t vb = value_bytes(A->dtype);
     int64_t *nprod, *row_size, *cbar_off, *rp;
+    mem.reserve(row_workspace_bytes(m));
     if ((rc = get(mem, nprod, (size_t)std::max<int64_t>(m, 1), "row nprod"))) return rc;
     if ((rc = get(mem, row_size, (size_t)std::max<int64_t>(m, 1), "row sizes"))) return rc;
     if ((rc = get(mem, cbar_off, (size_t)m + 1, "C_bar offsets"))) return rc;
@@ -711,8 +757,8 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     int32_t *ccol = nullptr;
     void *cval = nullptr;
     if (budget == 0 || (size_t)std::max<int64_t>(total, 1) * per <= budget) {
-        ccol = static_cast<int32_t *>(mem.get((size_t)std::max<int64_t>(total, 1) * 4));
-        if (ccol) cval = mem.get((size_t)std::max<int64_t>(total, 1) * vb);
+        ccol = static_cast<int32_t *>(mem.get_direct((size_t)std::max<int64_t>(total, 1) * 4));
+        if (ccol) cval = mem.get_direct((size_t)std::max<int64_t>(total, 1) * vb);
         if (!ccol || !cval) {
             // the whole C_bar does not fit: row chunks of a quarter of what is free
             mem.free_one(ccol);
@@ -736,7 +782,7 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     j.err = err;
     if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
     // step 5: prefix sum of the row sizes, allocation of C
-    if ((rc = get(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
+    if ((rc = get_own(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
     {
         PhaseScope ps(kPhScan, mem.st);
         BRM_CUDA(launch_scan(row_size, rp, m, tmp, mem.st));
@@ -745,8 +791,8 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     BRM_CUDA(cudaMemcpyAsync(&nnz, rp + m, sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));
     int32_t *col;
-    if ((rc = get(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
-    void *val = mem.get((size_t)std::max<int64_t>(nnz, 1) * vb);
+    if ((rc = get_own(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
+    void *val = mem.get_direct((size_t)std::max<int64_t>(nnz, 1) * vb);
     if (!val) return fail(BRM_ERR_OOM, "allocation of C.val failed");
     // step 6: copy C_bar into C
     {
@@ -876,11 +922,12 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     b->count = count;
     int rc = batch_setup(b->mem, count, A, B, b->o, b->src, b->row0);
     const int64_t M = b->src.m;
-    if (!rc) rc = get(b->mem, b->rp, (size_t)M + 1, "C.row_ptr");
+    if (!rc) rc = get_own(b->mem, b->rp, (size_t)M + 1, "C.row_ptr");
+    if (!rc) b->mem.reserve(row_workspace_bytes(M));
     if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz, &b->pb);
-    if (!rc) rc = get(b->mem, b->col, (size_t)std::max<int64_t>(b->nnz, 1), "C.col_idx");
+    if (!rc) rc = get_own(b->mem, b->col, (size_t)std::max<int64_t>(b->nnz, 1), "C.col_idx");
     if (!rc) {
-        b->val = b->mem.get((size_t)std::max<int64_t>(b->nnz, 1) * value_bytes(b->src.dtype));
+        b->val = b->mem.get_direct((size_t)std::max<int64_t>(b->nnz, 1) * value_bytes(b->src.dtype));
         if (!b->val) rc = fail(BRM_ERR_OOM, "allocation of C.val failed");
     }
     if (!rc) rc = get(b->mem, b->err, 1, "error flag");
@@ -1014,6 +1061,7 @@ int brm_spgemm_symbolic(const brm_csr *A, const brm_csr *B, int64_t *C_row_ptr, 
     const brm_options o = resolve(opts);
     Mem mem(alloc, static_cast<cudaStream_t>(stream));
     if (o.validate && (rc = validate_inputs(mem, A, B))) return rc;
+    mem.reserve(row_workspace_bytes(A->rows));
     Plan pl;
     rc = symbolic_into(mem, src_of(A, B), o, pl, C_row_ptr, nnz_C);
     g_trace.flush();
@@ -1038,6 +1086,7 @@ int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row
     if (dB_val && B->nnz > 0) BRM_CUDA(cudaMemsetAsync(dB_val, 0, (size_t)B->nnz * vb, st));
     BackwardArgs a{};
     a.m = A->rows;
+    a.nnz_a = A->nnz;
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.aval = A->val;

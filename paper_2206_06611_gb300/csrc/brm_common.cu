@@ -44,6 +44,7 @@ __global__ void k_bin(BinArgs a) {
         }
         const int s = arp[li], e = arp[li + 1];
         L = e - s;
+#pragma unroll 4
         for (int p = s; p < e; ++p) {
             const int k = acol[p];
             np += brp[k + 1] - brp[k];

@@ -117,7 +117,7 @@ cudaError_t launch_compact(int64_t m, const int64_t *cbar_off, const int64_t *rp
 
 // Backward pass of C = A * B (brm_backward.cu).
 struct BackwardArgs {
-    int64_t m;
+    int64_t m, nnz_a;
     const int32_t *arp, *acol; const void *aval;
     const int32_t *brp, *bcol; const void *bval;
     const int64_t *crp; const int32_t *ccol; const void *dC;
