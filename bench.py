@@ -336,18 +336,45 @@ def run_gpu(args):
 
 
 def run_profile(args):
-    """One warm-up call and one timed call of the workload, nothing else (the
-    command ncu captures)."""
+    """A short fixed sequence of calls for ncu to capture (no timing):
+    er       two BRMerge-Precise calls on the ER workload (n = --profile-n);
+    rmat     two BRMerge-Precise calls on R-MAT of scale --scale;
+    batched  a prepared batch of the 512-product mix, its numeric pass twice,
+             then one brm_spgemm_batched call;
+    diff     the differentiable workload's forward and backward once each."""
     import torch
     from paper_2206_06611_gb300 import brm
     torch.cuda.set_device(0)
-    A = I.erdos_renyi(args.profile_n, 16)
-    dA = brm.to_device(A, device="cuda:0")
-    for _ in range(2):
-        C = brm.brm_spgemm_precise(dA, dA)
+    if args.workload == "batched":
+        mats = I.batched_mix(512)
+        dev = [brm.to_device(M) for M in mats]
+        b = brm.Batch(dev, dev)
+        for _ in range(2):
+            b.numeric()
+            torch.cuda.synchronize()
+        C, _ = brm.brm_spgemm_batched(dev, dev)
         torch.cuda.synchronize()
-        del C
-    print(json.dumps({"profile": "ER", "n": A.rows, "launches": brm.brm_kernel_launches()}), flush=True)
+        info = {"profile": "batched", "nnz_C": C.nnz}
+    elif args.workload == "diff":
+        A = I.normal_values(I.rmat(18, 16), 101)
+        B = I.normal_values(I.erdos_renyi(1 << 18, 8), 102)
+        dA, dB = brm.to_device(A), brm.to_device(B)
+        a_val = dA.val.clone().requires_grad_(True)
+        C = brm.spgemm(brm.DeviceCSR(A.rows, A.cols, dA.rp, dA.col, a_val), dB)
+        G = torch.from_numpy(I.rand_normal(103, I.S_GRAD, np.arange(C.nnz)).astype(np.float32)).cuda()
+        (C.val * G).sum().backward()
+        torch.cuda.synchronize()
+        info = {"profile": "diff", "nnz_C": C.nnz}
+    else:
+        A = I.rmat(args.scale, 16) if args.workload == "rmat" else I.erdos_renyi(args.profile_n, 16)
+        dA = brm.to_device(A, device="cuda:0")
+        for _ in range(2):
+            C = brm.brm_spgemm_precise(dA, dA)
+            torch.cuda.synchronize()
+            del C
+        info = {"profile": args.workload, "n": A.rows}
+    info["launches"] = brm.brm_kernel_launches()
+    print(json.dumps(info), flush=True)
 
 
 # ---------------------------------------------------------------------------

@@ -93,7 +93,10 @@ typedef struct {
     void *ctx;
 } brm_allocator;
 
-/* Tuning and checking options; brm_options_default() fills the defaults.
+/* Tuning and checking options; brm_options_default() fills the defaults
+ * (start from it: a zeroed struct is valid too, but switches reg_top,
+ * reg_perm, reg_num_half and reg_num_direct off and takes the other
+ * defaults).
  *   validate       1: check both inputs on the device first (row_ptr starts at
  *                  0, is non-decreasing and ends at nnz; columns in range and
  *                  strictly ascending per row) and return BRM_ERR_INVALID.
@@ -123,6 +126,9 @@ typedef struct {
  *   reg_num_half   1 (default): with reg_perm, the numeric pass runs each
  *                  register row with twice the threads and half the keys of
  *                  its bin where it can (rows of <= 16 threads, >= 16 keys);
+ *   reg_num_direct 1 (default): with reg_perm, rows of 32-key register bins
+ *                  (the top bin among them) read their products from B at
+ *                  output time instead of staging them in shared memory;
  *   symbolic_hash  register bins count a row's distinct columns in the
  *                  symbolic pass with the numeric pass's sorting network on
  *                  bare columns (0, default) or by hashing into a
@@ -156,6 +162,7 @@ typedef struct {
     int32_t reg_top;
     int32_t reg_perm;
     int32_t reg_num_half;
+    int32_t reg_num_direct;
     size_t arena_bytes;
     size_t upper_chunk_bytes;
 } brm_options;

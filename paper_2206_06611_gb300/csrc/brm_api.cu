@@ -246,6 +246,7 @@ brm_options resolve(const brm_options *o) {
     r.reg_top = r.reg_top != 0 ? 1 : 0;
     r.reg_perm = r.reg_perm != 0 ? 1 : 0;
     r.reg_num_half = r.reg_num_half != 0 ? 1 : 0;
+    r.reg_num_direct = r.reg_num_direct != 0 ? 1 : 0;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -496,6 +497,7 @@ RowJob base_job(const Src &src, const brm_options &o) {
     j.reg_warps = o.reg_warps;
     j.sym_hash = o.symbolic_hash ? 1 : 0;
     j.num_half = o.reg_num_half ? 1 : 0;
+    j.num_direct = o.reg_num_direct ? 1 : 0;
     j.arp = src.arp;
     j.acol = src.acol;
     j.aval = src.aval;
@@ -1028,6 +1030,7 @@ void brm_options_default(brm_options *o) {
     o->reg_top = 1;
     o->reg_perm = 1;
     o->reg_num_half = 1;
+    o->reg_num_direct = 1;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
 }

@@ -34,21 +34,56 @@ __global__ void k_bin(BinArgs a) {
     const int lane = threadIdx.x & 31;
     int L = 0, bin = -1;
     int64_t np = 0;
+    // short rows: one thread per row; a warp with a row of more than 64
+    // entries instead takes its 32 rows one after another, each row's entries
+    // spread over the lanes, lane r keeping row r's sum (rows of power-law
+    // matrices differ by orders of magnitude in length)
+    const int32_t *arp_i = a.arp, *acol_i = a.acol, *brp_i = a.brp;
+    int s_i = 0, e_i = 0;
     if (i < a.m) {
-        const int32_t *arp = a.arp, *acol = a.acol, *brp = a.brp;
         int64_t li = i;
         if (a.prods != nullptr) {
             const ProdDesc &d = a.prods[a.prod_of[i]];
-            arp = d.arp; acol = d.acol; brp = d.brp;
+            arp_i = d.arp; acol_i = d.acol; brp_i = d.brp;
             li = i - d.row0;
         }
-        const int s = arp[li], e = arp[li + 1];
-        L = e - s;
+        s_i = arp_i[li];
+        e_i = arp_i[li + 1];
+    }
+    if (!__any_sync(kFull, e_i - s_i > 64)) {
+        L = e_i - s_i;
 #pragma unroll 4
-        for (int p = s; p < e; ++p) {
-            const int k = acol[p];
-            np += brp[k + 1] - brp[k];
+        for (int p = s_i; p < e_i; ++p) {
+            const int k = acol_i[p];
+            np += brp_i[k + 1] - brp_i[k];
         }
+    } else {
+        const int64_t wbase = i - lane;
+        for (int r = 0; r < 32; ++r) {
+            const int64_t ir = wbase + r;
+            if (ir >= a.m) break;
+            const int32_t *arp = a.arp, *acol = a.acol, *brp = a.brp;
+            int64_t li = ir;
+            if (a.prods != nullptr) {
+                const ProdDesc &d = a.prods[a.prod_of[ir]];
+                arp = d.arp; acol = d.acol; brp = d.brp;
+                li = ir - d.row0;
+            }
+            const int s = arp[li], e = arp[li + 1];
+            int64_t part = 0;
+            for (int p = s + lane; p < e; p += 32) {
+                const int k = acol[p];
+                part += brp[k + 1] - brp[k];
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(kFull, part, d);
+            if (lane == r) {
+                np = part;
+                L = e - s;
+            }
+        }
+    }
+    if (i < a.m) {
         // threads per row a register bin would need: enough for the products
         // (E per thread) and for the lists (E/4 per thread)
         const int E = a.reg_keys, EL = a.reg_keys / kRegKeysPerList;

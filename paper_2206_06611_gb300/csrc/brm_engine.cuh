@@ -193,6 +193,7 @@ struct RowJob {
     uint16_t *perm;
     const int64_t *perm_off;    // per row: where its order starts in perm
     int32_t num_half;           // numeric from a recorded order: half the keys, twice the threads
+    int32_t num_direct;         // numeric from a recorded order, 32-key rows: products read from B directly
     // long rows only: per slot, the arena offset (bytes) and the product count
     char *arena;
     const int64_t *arena_off;

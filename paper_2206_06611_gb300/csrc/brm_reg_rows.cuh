@@ -697,6 +697,173 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
     }
 }
 
+// The same numeric pass from a recorded order without staging the products:
+// every run start reads its products straight from B (list index by a search
+// in the list ends, B position, column and value), eight output positions
+// at a time so that their loads are in flight together.  Only the list
+// descriptors use shared memory, so many more warps fit an SM; used for the
+// rows of 32-key bins, whose staged form is limited by shared memory.
+template <class P>
+__device__ __noinline__ typename P::T perm_tree_reduce_direct(const uint16_t *pr, int P0, int N, const int32_t *d_off,
+                                                              const int32_t *d_q0, const typename P::In *d_a, int L,
+                                                              const typename P::In *bval) {
+    using T = typename P::T;
+    T V[kRegMaxDepth];
+    int G[kRegMaxDepth];
+    int nv = 0, prev_l = 0;
+    for (int pos = P0; pos < N; ++pos) {
+        const uint32_t pe = pr[pos];
+        if (pos > P0 && (pe & kPermStart)) break;
+        const int p = (int)(pe & kPermPos);
+        const int l = find_last_le(d_off, L, p);
+        if (nv > 0) {
+            const int d = 32 - __clz(prev_l ^ l);
+            while (nv > 1 && G[nv - 1] < d) {
+                V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+                --nv;
+            }
+            G[nv] = d;
+        }
+        if (nv == kRegMaxDepth) {   // only reachable with duplicate columns inside a B row (invalid input)
+            V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+            --nv;
+        }
+        V[nv++] = P::mul(d_a[l], bval[d_q0[l] + (p - d_off[l])]);
+        prev_l = l;
+    }
+    while (nv > 1) {
+        V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+        --nv;
+    }
+    return V[0];
+}
+
+template <class P, int TPR, int E>
+__global__ void __launch_bounds__(256) k_rows_perm_direct(RowJob j) {
+    using Cf = RegCfg<TPR, E>;
+    using In = typename P::In;
+    using T = typename P::T;
+    using Out = typename P::Out;
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int NB = 8;   // output positions whose loads are issued together
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int rho = lane / TPR, t = lane % TPR, rowbase = rho * TPR;
+    unsigned char *desc = smem + (size_t)wid * reg_stage_bytes(E) + (size_t)rho * Cf::DESC;
+    In *d_a = reinterpret_cast<In *>(desc);
+    int32_t *d_q0 = reinterpret_cast<int32_t *>(desc + 8 * Cf::LCAP);
+    int32_t *d_off = reinterpret_cast<int32_t *>(desc + 12 * Cf::LCAP);
+    const uint64_t keep = l2_keep_policy();
+    const int stride = gridDim.x * nwarps * Cf::RPW;
+
+    for (int r0 = (blockIdx.x * nwarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
+        const int slot = r0 + rho;
+        const bool has_row = slot < j.count;
+        const int row = has_row ? j.rows[slot] : 0;
+        RowIn<In> ri{};
+        if (has_row) ri = row_in<In>(j, row);
+        const int L = has_row ? ri.L : 0;
+        const uint16_t *pr = j.perm + (has_row ? j.perm_off[row] : 0);
+
+        int carry = 0;
+        for (int c0 = 0; __any_sync(kFull, c0 < L); c0 += TPR) {
+            const int l = c0 + t;
+            int len = 0;
+            if (l < L) {
+                const int k = ri.acol[l];
+                const int q0 = ri.brp[k];
+                len = ri.brp[k + 1] - q0;
+                d_q0[l] = q0;
+                d_a[l] = ri.aval[l];
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < TPR; d <<= 1) {
+                const int u = __shfl_up_sync(kFull, incl, d, TPR);
+                if (t >= d) incl += u;
+            }
+            if (l < L) d_off[l + 1] = carry + incl;
+            carry += __shfl_sync(kFull, incl, TPR - 1, TPR);
+        }
+        if (t == 0) d_off[0] = 0;
+        const int N = carry;
+        __syncwarp();
+
+        const int64_t obase = has_row ? j.out_rp[row] : 0;
+        const int cap = has_row ? (int)(j.out_rp[row + 1] - obase) : 0;
+        int32_t *ocol = j.out_col + obase;
+        Out *oval = static_cast<Out *>(j.out_val) + obase;
+        const unsigned gmask = (TPR == 32) ? kFull : (((1u << TPR) - 1u) << rowbase);
+        const unsigned lt = (1u << lane) - 1u;
+        int count = 0;
+        for (int j0 = 0; __any_sync(kFull, j0 * TPR < N); j0 += NB) {
+            uint32_t e[NB];
+            int q[NB], l[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int pos = (j0 + b) * TPR + t;
+                e[b] = pos < N ? __ldcs(pr + pos) : 0u;
+                l[b] = 0;
+                q[b] = 0;
+                if (e[b] & kPermStart) {
+                    const int p0 = (int)(e[b] & kPermPos);
+                    l[b] = find_last_le(d_off, L, p0);
+                    q[b] = d_q0[l[b]] + (p0 - d_off[l[b]]);
+                }
+            }
+            int32_t c[NB];
+            In v[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                c[b] = 0;
+                v[b] = In();
+                if (e[b] & kPermStart) {
+                    c[b] = ld_keep(ri.bcol + q[b], keep);
+                    v[b] = ld_keep(ri.bval + q[b], keep);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const bool start = (e[b] & kPermStart) != 0;
+                const unsigned msk = __ballot_sync(kFull, start) & gmask;
+                if (start) {
+                    const int w = count + __popc(msk & lt);
+                    T val;
+                    if (!(e[b] & kPermMulti)) val = P::mul(d_a[l[b]], v[b]);
+                    else val = perm_tree_reduce_direct<P>(pr, (j0 + b) * TPR + t, N, d_off, d_q0, d_a, L, ri.bval);
+                    if (w < cap) {
+                        __stcs(ocol + w, c[b]);
+                        __stcs(oval + w, P::fin(val));
+                    }
+                }
+                count += __popc(msk);
+            }
+        }
+        if (has_row) {
+            if (t == 0 && (count > cap || (j.exact && count != cap))) atomicOr(j.err, 1u);
+            if (t == 0 && j.out_cnt != nullptr) j.out_cnt[row] = count;
+        }
+        __syncwarp();   // the descriptors are reused by the next rows
+    }
+}
+
+template <class P, int TPR, int E>
+cudaError_t launch_perm_direct_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
+    const size_t sm = (size_t)warps * reg_stage_bytes(E);
+    auto kern = k_rows_perm_direct<P, TPR, E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm);
+    if (e != cudaSuccess) return e;
+    const int rows_per_block = warps * RegCfg<TPR, E>::RPW;
+    const int need = (j.count + rows_per_block - 1) / rows_per_block;
+    const int grid = max(1, min(need, sms * max(occ, 1)));
+    kern<<<grid, warps * 32, sm, st>>>(j);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 template <class P, int TPR, int E>
 cudaError_t launch_perm_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
     const size_t sm = (size_t)warps * perm_warp_bytes<E, P>();
@@ -726,6 +893,8 @@ cudaError_t launch_reg_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
             // products and lists per row): more warps in flight for the gathers
             if constexpr (TPR <= 16 && E >= 16)
                 if (j.num_half) return launch_perm_t<P, 2 * TPR, E / 2>(j, st, sms, warps);
+            if constexpr (E >= 32)
+                if (j.num_direct) return launch_perm_direct_t<P, TPR, E>(j, st, sms, warps);
             return launch_perm_t<P, TPR, E>(j, st, sms, warps);
         }
     }

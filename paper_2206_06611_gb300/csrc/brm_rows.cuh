@@ -22,7 +22,10 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockThreads = 256;
 constexpr int kBlockK = 8;
 constexpr int kLongThreads = 512;
-constexpr int kLongK = 8;
+// diagonals per thread in the long-row kernel: the value passes use 4 (so
+// that two 512-thread blocks fit an SM), the index-only symbolic pass 8
+template <class P>
+__host__ __device__ constexpr int long_k() { return P::kVal ? 4 : 8; }
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -100,7 +103,7 @@ template <class P>
 __host__ __device__ constexpr size_t long_row_bytes(int64_t n, int64_t L) { return long_layout<P>(n, L).total; }
 
 template <class P>
-__global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
+__global__ void __launch_bounds__(kLongThreads, 2) k_rows_long(RowJob j) {
     __shared__ int ws[kLongThreads / 32 + 1];
     BlockGrp<kLongThreads> g;
     g.ws = ws;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kLongThreads) k_rows_long(RowJob j) {
         b1.col = reinterpret_cast<int32_t *>(p + lay.col1);
         b0.off = reinterpret_cast<int32_t *>(p + lay.off0);
         b1.off = reinterpret_cast<int32_t *>(p + lay.off1);
-        brm_row<P, BlockGrp<kLongThreads>, kLongK, 4>(g, row, j, b0, b1);
+        brm_row<P, BlockGrp<kLongThreads>, long_k<P>(), 4>(g, row, j, b0, b1);
     }
 }
 

@@ -129,6 +129,7 @@ def test_register_bins_every_size(mode, dtype, comp):
         for keys in (8, 16, 32):
             assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys), ref)
             assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys, reg_perm=False), ref)
+            assert_rows_exact(run(A, Bm, "precise", dtype, comp, reg_keys=keys, reg_num_direct=False), ref)
             assert_rows_exact(run(A, Bm, "upper", dtype, comp, reg_keys=keys), ref)
 
 
