@@ -140,6 +140,15 @@ typedef struct {
  *   block_max_nprod rows up to this many products are merged by one thread
  *                  block in shared memory; longer rows use the device-memory
  *                  ping-pong arena (bounded by the kernel's shared memory).
+ *   long_bucket    1: rows beyond block_max_nprod are merged by column
+ *                  buckets in the numeric pass -- their products are
+ *                  scattered to column cells in the arena and every column is
+ *                  reduced in the merge tree's order (the same values as the
+ *                  merge rounds) -- when every such row has at most 65535
+ *                  lists and B at most 2^24 columns; 0 (default): merge rounds
+ *                  through the device-memory arena.  (The symbolic pass always
+ *                  counts those rows' columns in a shared-memory bitmap when B
+ *                  has at most 2^24 columns.)
  *   arena_bytes    budget of the device-memory arena for long rows (0 = the
  *                  library picks 1/8 of free memory, at least enough for the
  *                  longest row).
@@ -163,6 +172,7 @@ typedef struct {
     int32_t reg_perm;
     int32_t reg_num_half;
     int32_t reg_num_direct;
+    int32_t long_bucket;
     size_t arena_bytes;
     size_t upper_chunk_bytes;
 } brm_options;

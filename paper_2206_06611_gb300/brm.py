@@ -54,6 +54,7 @@ class brm_options(ctypes.Structure):
                 ("reg_max_nprod", ctypes.c_int32), ("reg_keys", ctypes.c_int32), ("reg_warps", ctypes.c_int32),
                 ("symbolic_hash", ctypes.c_int32), ("reg_top", ctypes.c_int32), ("reg_perm", ctypes.c_int32),
                 ("reg_num_half", ctypes.c_int32), ("reg_num_direct", ctypes.c_int32),
+                ("long_bucket", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_size_t),
                 ("upper_chunk_bytes", ctypes.c_size_t)]
 
@@ -246,7 +247,7 @@ def _stream(stream=None):
 
 def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
             reg_keys=0, reg_warps=0, symbolic_hash=False, reg_top=True, reg_perm=True, reg_num_half=True,
-            reg_num_direct=True, arena_bytes=0, upper_chunk_bytes=0) -> brm_options:
+            reg_num_direct=True, long_bucket=False, arena_bytes=0, upper_chunk_bytes=0) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -266,6 +267,7 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
     o.reg_perm = int(bool(reg_perm))
     o.reg_num_half = int(bool(reg_num_half))
     o.reg_num_direct = int(bool(reg_num_direct))
+    o.long_bucket = int(bool(long_bucket))
     o.arena_bytes = arena_bytes
     o.upper_chunk_bytes = upper_chunk_bytes
     return o

@@ -247,6 +247,7 @@ brm_options resolve(const brm_options *o) {
     r.reg_perm = r.reg_perm != 0 ? 1 : 0;
     r.reg_num_half = r.reg_num_half != 0 ? 1 : 0;
     r.reg_num_direct = r.reg_num_direct != 0 ? 1 : 0;
+    r.long_bucket = r.long_bucket != 0 ? 1 : 0;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -399,19 +400,27 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
 // Device-memory arena of the long rows of one pass: the long slots (longest
 // first) cut into batches whose ping-pong slices fit the budget.
 struct LongPlan {
+    bool bucket = false;            // column-bucket kernels (else merge rounds)
     std::vector<int64_t> starts;    // batch boundaries over the long slots
     int64_t *off_d = nullptr;       // device: arena offset of every long slot
     char *arena = nullptr;
 };
 
-int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, LongPlan &lp) {
+int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp) {
     const int64_t nl = (int64_t)pl.long_rows_h.size();
     lp.starts.clear();
     if (nl == 0) return BRM_OK;
+    // the symbolic pass counts long rows with the column bitmap whenever B has
+    // at most 2^24 columns; the numeric pass uses column buckets on request
+    // (they pack a list index into 16 bits and cut B's columns into at most
+    // 4096 cells of at most 4096 columns)
+    int64_t maxL = 0;
+    for (int64_t s = 0; s < nl; ++s) maxL = std::max<int64_t>(maxL, pl.long_L_h[s]);
+    lp.bucket = bcols <= kLbMaxCols && (v == kIdx || (o.long_bucket && maxL <= kLbMaxL));
     std::vector<int64_t> need(nl);
     size_t biggest = 0;
     for (int64_t s = 0; s < nl; ++s) {
-        need[s] = (int64_t)long_row_bytes_for(v, pl.long_nprod_h[s], pl.long_L_h[s]);
+        need[s] = (int64_t)long_row_bytes_for(v, pl.long_nprod_h[s], pl.long_L_h[s], lp.bucket);
         biggest = std::max(biggest, (size_t)need[s]);
     }
     size_t budget = o.arena_bytes;
@@ -459,6 +468,7 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         RowJob jb = j;
         jb.rows = pl.long_rows_s + lp.starts[bi];
         jb.count = (int32_t)(lp.starts[bi + 1] - lp.starts[bi]);
+        jb.long_bucket = lp.bucket ? 1 : 0;
         jb.arena = lp.arena;
         jb.arena_off = lp.off_d + lp.starts[bi];
         jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
@@ -470,7 +480,7 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
 // One BRMerge pass (symbolic or numeric) over all bins.
 int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
     LongPlan lp;
-    int rc = plan_long(mem, v, pl, o, lp);
+    int rc = plan_long(mem, v, pl, o, j.bcols, lp);
     if (rc) return rc;
     if ((rc = launch_pass(v, pl, lp, j, mem.st, true))) return rc;
     if (lp.arena) {
@@ -498,6 +508,7 @@ RowJob base_job(const Src &src, const brm_options &o) {
     j.sym_hash = o.symbolic_hash ? 1 : 0;
     j.num_half = o.reg_num_half ? 1 : 0;
     j.num_direct = o.reg_num_direct ? 1 : 0;
+    j.bcols = src.bcols;
     j.arp = src.arp;
     j.acol = src.acol;
     j.aval = src.aval;
@@ -934,7 +945,7 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     }
     if (!rc) rc = get(b->mem, b->err, 1, "error flag");
     b->v = value_kind(b->src.dtype, b->o);
-    if (!rc) rc = plan_long(b->mem, b->v, b->pl, b->o, b->lp);
+    if (!rc) rc = plan_long(b->mem, b->v, b->pl, b->o, b->src.bcols, b->lp);
     if (rc) {
         delete b;
         return rc;
@@ -1031,6 +1042,7 @@ void brm_options_default(brm_options *o) {
     o->reg_perm = 1;
     o->reg_num_half = 1;
     o->reg_num_direct = 1;
+    o->long_bucket = 0;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
 }

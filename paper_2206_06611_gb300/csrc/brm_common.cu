@@ -381,10 +381,10 @@ extern cudaError_t launch_rows_f64(int bin, const RowJob &j, cudaStream_t st);
 extern cudaError_t launch_rows_f32(int bin, const RowJob &j, cudaStream_t st);
 extern cudaError_t launch_rows_f32c(int bin, const RowJob &j, cudaStream_t st);
 extern cudaError_t launch_rows_idx(int bin, const RowJob &j, cudaStream_t st);
-extern size_t long_bytes_f64(int64_t n, int64_t L);
-extern size_t long_bytes_f32(int64_t n, int64_t L);
-extern size_t long_bytes_f32c(int64_t n, int64_t L);
-extern size_t long_bytes_idx(int64_t n, int64_t L);
+extern size_t long_bytes_f64(int64_t n, int64_t L, bool bucket);
+extern size_t long_bytes_f32(int64_t n, int64_t L, bool bucket);
+extern size_t long_bytes_f32c(int64_t n, int64_t L, bool bucket);
+extern size_t long_bytes_idx(int64_t n, int64_t L, bool bucket);
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st) {
     switch (v) {
@@ -395,12 +395,12 @@ cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st) {
     }
 }
 
-size_t long_row_bytes_for(VKind v, int64_t n, int64_t L) {
+size_t long_row_bytes_for(VKind v, int64_t n, int64_t L, bool bucket) {
     switch (v) {
-        case kF64: return long_bytes_f64(n, L);
-        case kF32: return long_bytes_f32(n, L);
-        case kF32C: return long_bytes_f32c(n, L);
-        default: return long_bytes_idx(n, L);
+        case kF64: return long_bytes_f64(n, L, bucket);
+        case kF32: return long_bytes_f32(n, L, bucket);
+        case kF32C: return long_bytes_f32c(n, L, bucket);
+        default: return long_bytes_idx(n, L, bucket);
     }
 }
 

@@ -33,6 +33,8 @@ namespace brm {
 
 constexpr int32_t kColEnd = 0x7fffffff;   // larger than any column index (< 2^31 - 1)
 
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 // ---------------------------------------------------------------------------
 // Value policies.  Products are rounded before any addition and additions are
 // never contracted into an FMA (explicit _rn intrinsics).
@@ -194,7 +196,11 @@ struct RowJob {
     const int64_t *perm_off;    // per row: where its order starts in perm
     int32_t num_half;           // numeric from a recorded order: half the keys, twice the threads
     int32_t num_direct;         // numeric from a recorded order, 32-key rows: products read from B directly
-    // long rows only: per slot, the arena offset (bytes) and the product count
+    // long rows only: 1 = column buckets (brm_long_rows.cuh), 0 = merge
+    // rounds in the arena; B's column count (the largest of a batch); per
+    // slot, the arena offset (bytes) and the product count
+    int32_t long_bucket;
+    int64_t bcols;
     char *arena;
     const int64_t *arena_off;
     const int64_t *slot_nprod;

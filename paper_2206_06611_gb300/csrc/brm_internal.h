@@ -48,6 +48,12 @@ constexpr int kWarpCap = 256;     // warp bin: nprod_i <= 256 and L_i <= 256
 constexpr int kBlockCap = 4096;   // block bin: nprod_i <= 4096 ...
 constexpr int kBlockLCap = 1024;  // ... and L_i <= 1024
 
+// Limits of the column-bucket long-row kernels (brm_long_rows.cuh): lists of
+// a row (a 16-bit list index that never forms the all-ones padding key) and
+// columns of B (at most 4096 cells of at most 4096 columns each).
+constexpr int kLbMaxL = 65535;
+constexpr int64_t kLbMaxCols = (int64_t)1 << 24;
+
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {
     kPhValidate = 0, kPhBin, kPhSymReg, kPhSymWarp, kPhSymBlock, kPhSymLong, kPhScan,
@@ -61,7 +67,7 @@ extern std::atomic<long long> g_launches;
 enum VKind { kIdx = 0, kF64 = 1, kF32 = 2, kF32C = 3 };
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st);
-size_t long_row_bytes_for(VKind v, int64_t nprod, int64_t L);
+size_t long_row_bytes_for(VKind v, int64_t nprod, int64_t L, bool bucket);
 
 // Statistics written by the binning kernels.
 struct BinStats {

@@ -5,13 +5,15 @@
 //              buffers and list offsets in the warp's slice of shared memory.
 //   block bin  nprod_i <= BCAP, L_i <= BLCAP: one thread block per row,
 //              buffers in shared memory.
-//   long bin   everything else: one thread block per row, buffers in a
-//              device-memory arena slice given per row by the host.
+//   long bin   everything else: one thread block per row; by column buckets
+//              (brm_long_rows.cuh) or by merge rounds in a device-memory
+//              arena slice given per row by the host (this file).
 // Rows are taken from the bin's row list in a grid-stride loop.
 #pragma once
 
 #include "brm_engine.cuh"
 #include "brm_internal.h"
+#include "brm_long_rows.cuh"
 #include "brm_reg_rows.cuh"
 
 namespace brm {
@@ -26,8 +28,6 @@ constexpr int kLongThreads = 512;
 // that two 512-thread blocks fit an SM), the index-only symbolic pass 8
 template <class P>
 __host__ __device__ constexpr int long_k() { return P::kVal ? 4 : 8; }
-
-__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory bytes of one row buffer pair holding `cap` elements and
 // `lcap` lists: two value arrays, two column arrays, two offset arrays.  The
@@ -171,12 +171,18 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
         return cudaGetLastError();
     }
     // long rows: one block per row of the batch
+    if (j.long_bucket) return launch_long_bucket<P>(j, st);
     k_rows_long<P><<<j.count, kLongThreads, 0, st>>>(j);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
+// Arena bytes of one long row: the bucket kernels (the symbolic one needs
+// none) or the merge rounds.
 template <class P>
-size_t long_bytes_t(int64_t n, int64_t L) { return long_row_bytes<P>(n, L); }
+size_t long_bytes_t(int64_t n, int64_t L, bool bucket) {
+    if (bucket) return P::kVal ? lb_layout<P>(n, L).total : 256;
+    return long_row_bytes<P>(n, L);
+}
 
 }  // namespace brm
