@@ -402,6 +402,10 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
 struct LongPlan {
     bool bucket = false;            // column-bucket kernels (else merge rounds)
     std::vector<int64_t> starts;    // batch boundaries over the long slots
+    // numeric bucket kernels, per batch: where its work list starts in the
+    // arena (after its rows), and its capacity in records
+    std::vector<int64_t> work_off, work_cap;
+    int64_t slots_bytes = 0, work_bytes_max = 0;
     int64_t *off_d = nullptr;       // device: arena offset of every long slot
     char *arena = nullptr;
 };
@@ -442,6 +446,30 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
         maxbatch = std::max(maxbatch, cur);
     }
     lp.starts.push_back(nl);
+    lp.work_off.clear();
+    lp.work_cap.clear();
+    if (lp.bucket && v != kIdx) {
+        // after each batch's rows: its work list, two counters, and the value
+        // slots of the work-list kernel's blocks
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t vb = v == kF32 ? 4 : 8;
+        lp.slots_bytes = (int64_t)align_up((size_t)kLbHotPerSm * std::max(sms, 1) * kLbSlots * vb, 256);
+        maxbatch = 0;
+        for (size_t b = 0; b + 1 < lp.starts.size(); ++b) {
+            int64_t cap = 0, rows = 0;
+            for (int64_t s = lp.starts[b]; s < lp.starts[b + 1]; ++s) {
+                cap += lb_work_cap(pl.long_nprod_h[s]);
+                rows = off[s] + need[s];
+            }
+            const int64_t wo = (int64_t)align_up((size_t)rows, 256);
+            lp.work_off.push_back(wo);
+            lp.work_cap.push_back(cap);
+            const size_t wb = align_up((size_t)cap * kLbWorkBytes, 256) + 256;
+            maxbatch = std::max(maxbatch, (size_t)wo + wb + (size_t)lp.slots_bytes);
+        }
+    }
     int rc = get(mem, lp.off_d, nl, "arena offsets");
     if (rc) return rc;
     if ((rc = get(mem, lp.arena, maxbatch, "long-row arena"))) return rc;
@@ -471,6 +499,14 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         jb.long_bucket = lp.bucket ? 1 : 0;
         jb.arena = lp.arena;
         jb.arena_off = lp.off_d + lp.starts[bi];
+        if (bi < lp.work_off.size()) {
+            char *w = lp.arena + lp.work_off[bi];
+            const size_t wb = align_up((size_t)lp.work_cap[bi] * kLbWorkBytes, 256);
+            jb.lb_work = w;
+            jb.lb_ctr = reinterpret_cast<int32_t *>(w + wb);
+            jb.lb_slots = w + wb + 256;
+            jb.lb_cap = lp.work_cap[bi];
+        }
         jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
         BRM_CUDA(launch_rows(v, kBinLong, jb, st));
     }

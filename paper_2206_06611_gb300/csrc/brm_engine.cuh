@@ -201,6 +201,12 @@ struct RowJob {
     // slot, the arena offset (bytes) and the product count
     int32_t long_bucket;
     int64_t bcols;
+    // numeric bucket kernels: the batch's work list (lb_cap records), its two
+    // counters (records written, records taken) and the giant-column slots
+    void *lb_work;
+    int32_t *lb_ctr;
+    void *lb_slots;
+    int64_t lb_cap;
     char *arena;
     const int64_t *arena_off;
     const int64_t *slot_nprod;

@@ -53,6 +53,15 @@ constexpr int kBlockLCap = 1024;  // ... and L_i <= 1024
 // columns of B (at most 4096 cells of at most 4096 columns each).
 constexpr int kLbMaxL = 65535;
 constexpr int64_t kLbMaxCols = (int64_t)1 << 24;
+// The numeric bucket kernels' work list (hot cells and giant columns, each of
+// more than kLbUnit products: at most n / (kLbUnit + 1) + 1 records for a row
+// of n products, kLbWorkBytes each) and the value slots of a giant column
+// (kLbSlots per block of the work-list kernel, kLbHotPerSm blocks per SM).
+constexpr int kLbUnit = 256;
+constexpr size_t kLbWorkBytes = 32;
+constexpr int kLbSlots = 65536;
+constexpr int kLbHotPerSm = 2;
+__host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUnit + 1) + 1; }
 
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {

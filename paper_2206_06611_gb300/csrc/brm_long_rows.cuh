@@ -1,4 +1,4 @@
-// Long rows by column buckets (the default long-row path).
+// Long rows by column buckets.
 //
 // Algorithm 1 fixes every value of a row column by column: the value at
 // column c is the sum of the products A_it * B_tc over the lists t whose B
@@ -9,34 +9,38 @@
 // procedure that adds the products of each column in that aligned binary tree
 // gives Algorithm 1's result bit for bit, whatever order the columns are
 // visited in.  The merge rounds of the arena kernel read and write a long row
-// once per round; here a row is read twice and its products are written and
-// read once.
+// once per round; here a row is read three times and its products are written
+// and read once (twice in hot cells).
 //
 // Symbolic pass (column counts only): the row's columns are set in a
 // shared-memory bitmap (one window of 2^20 columns at a time) and counted.
 //
-// Numeric pass, one thread block per row:
-//  1. histogram: the row's products are counted per cell of 2^sh columns
-//     (at most 4096 cells cover B's columns);
-//  2. plan: consecutive cells are grouped into units of at most 256
-//     products: a cut wherever the running count crosses a multiple of 128,
-//     before and after every cell of more than 128 products, and at every
-//     aligned window of 2^16 columns;
-//  3. scatter: every product goes to its cell's region of a device-memory
-//     arena as a 32-bit key (the column's low 16 bits above the list index)
-//     and its rounded value;
-//  4. units in column order, one warp per unit, 16 units at a time: the
-//     warp sorts its unit's keys (and values) in registers with a bitonic
-//     network (8 per lane), and every run of equal columns is reduced in tree
-//     order -- by one lane with a stack of partial sums when short; when
-//     long, each lane reduces an aligned range of lists and the lanes'
-//     results are combined as the five tree levels above them; the warps'
-//     column counts give the units' output offsets;
-//  5. a single cell of more than 256 products is split again by column (its
-//     products are counted per column, planned into units the same way and
-//     copied to a second arena region in column order); a column of more than
-//     256 products is reduced densely: its values go to one slot per list and
-//     the tree is evaluated over the slots by the block.
+// Numeric pass, per batch of long rows, three kernels:
+//  0. the bitmap kernel again, writing every row's distinct-column count per
+//     cell of 2^sh columns (at most 4096 cells cover B's columns), so that
+//     every cell's place in the row's output is known in advance;
+//  1. one thread block per row:
+//     a. histogram: the row's products are counted per cell;
+//     b. plan: consecutive cells are grouped into units of at most 256
+//        products -- a cut wherever the running count crosses a multiple of
+//        128, before and after every cell of more than 128 products, and at
+//        every aligned window of 2^16 columns;
+//     c. scatter: every product goes to its cell's region of a device-memory
+//        arena as a 32-bit key (the column's low 16 bits above the list
+//        index) and its rounded value;
+//     d. units, taken by the warps one at a time: the warp sorts its unit's
+//        keys and values in registers with a bitonic network (8 per lane) and
+//        reduces every run of equal columns in tree order -- by one lane
+//        with a stack of partial sums when short; when long, each lane
+//        reduces an aligned range of lists and the lanes' results are
+//        combined as the five tree levels above them -- writing at the
+//        unit's known place; a unit of a single cell of more than 256
+//        products goes to a work list;
+//  2. persistent thread blocks take the work list: a hot cell is counted per
+//     column, planned into units the same way, copied column by column to a
+//     second arena region, and its units are taken by the warps; a column of
+//     more than 256 products ("giant") is reduced by the block densely: its
+//     values go to one slot per list and the tree is evaluated over the slots.
 // A row qualifies when it has at most 65535 lists and B at most 2^24 columns
 // (a key never equals the all-ones padding); the host otherwise keeps the
 // arena kernel for the whole pass.
@@ -51,20 +55,19 @@
 
 namespace brm {
 
-constexpr int kLsThreads = 1024;            // symbolic bitmap kernel
+constexpr int kLsThreads = 1024;            // bitmap kernel
 constexpr int kLsWinBits = 1 << 20;         // columns per bitmap window (128 KB)
-constexpr int kLbThreads = 512;             // numeric bucket kernel
-constexpr int kLbWarps = kLbThreads / 32;
+constexpr int kLbThreads = 512;             // row and work-list kernels
 constexpr int kLbCells = 4096;              // histogram cells of a row
-constexpr int kLbUnit = 256;                // products of a unit (one warp, 8 per lane)
 constexpr int kLbHalf = kLbUnit / 2;        // cut spacing of the plan
 constexpr int kLbRunShort = 32;             // runs up to this size: one lane reduces
-constexpr int kLbDepth = 18;                // partial-sum stack (tree height <= 16, +1)
+constexpr int kLbDepth = 18;                // giant column: partial-sum stack (tree height <= 16, +1)
 constexpr uint32_t kLbPad = 0xffffffffu;    // padding key, above every real key
 constexpr size_t kLbBmBytes = 8192;         // giant column: one bit per list (65536 lists)
 
 static_assert(kLbCells % kLbThreads == 0 && kLbThreads % 32 == 0, "bucket kernel: per-thread shares must be whole");
 static_assert(kLbMaxL <= 65535, "list index and column must never form the padding key");
+static_assert(kLbUnit == 256, "the warp sort holds 8 keys per lane");
 
 __host__ __device__ constexpr int lb_bitlen(uint64_t x) {
     int b = 0;
@@ -78,44 +81,25 @@ __host__ __device__ constexpr int lb_shift(int64_t ncols) {
     return b > 12 ? b - 12 : 0;
 }
 
-// Device-memory arena of one long row of the numeric bucket kernel: level-1
-// keys and values, level-2 keys and values (hot cells), one slot per list
-// (giant columns), and the level-2 plan of the cell being split.
+// Device-memory arena of one long row of the numeric bucket kernels: level-1
+// keys and values, level-2 keys and values (hot cells), and the row's
+// distinct-column count per cell.
 struct LbLayout {
-    size_t k1, v1, k2, v2, slots, meta, wmeta, defer, total;
+    size_t k1, v1, k2, v2, cells, total;
 };
-
-// Per warp, the state of the hot cell it is splitting: column ends, nonzero
-// columns before each column, cut marks.
-constexpr int kLbWmeta = 2 * 256 + 8;
-
-// Work deferred to the whole block: a giant column (level 1 or 2) or a hot
-// cell too wide for a warp.  Each holds more than kLbUnit products of its
-// own, so a row of n products defers at most n / 257 of them.
-struct LbDefer {
-    int32_t kind, st, m, pad;
-    int64_t col, ob;
-};
-constexpr int32_t kLbDeferGiant1 = 0, kLbDeferGiant2 = 1, kLbDeferHot = 2;
-
-__host__ __device__ constexpr int64_t lb_defer_cap(int64_t n) { return n / (kLbUnit + 1) + 1; }
 
 template <class P>
-__host__ __device__ constexpr LbLayout lb_layout(int64_t n, int64_t L) {
+__host__ __device__ constexpr LbLayout lb_layout(int64_t n) {
     using T = typename P::T;
     const size_t kb = align_up(sizeof(uint32_t) * (size_t)n, 256);
     const size_t vb = align_up(sizeof(T) * (size_t)n, 256);
-    const size_t sb = align_up(sizeof(T) * (size_t)(L > 0 ? L : 1), 256);
-    const size_t mb = align_up(sizeof(int32_t) * (size_t)(2 * kLbCells + 2), 256);
-    const size_t wb = align_up(sizeof(int32_t) * (size_t)kLbWmeta * (kLbThreads / 32), 256);
-    const size_t db = align_up(sizeof(LbDefer) * (size_t)lb_defer_cap(n), 256);
-    const size_t s0 = 2 * kb + 2 * vb;
-    return LbLayout{0, kb, kb + vb, 2 * kb + vb, s0, s0 + sb, s0 + sb + mb, s0 + sb + mb + wb, s0 + sb + mb + wb + db};
+    const size_t cb = align_up(sizeof(uint16_t) * (size_t)kLbCells, 256);
+    return LbLayout{0, kb, kb + vb, 2 * kb + vb, 2 * kb + 2 * vb, 2 * kb + 2 * vb + cb};
 }
 
-// Shared memory of the numeric bucket kernel (dynamic part).
+// Shared memory of the row kernel (dynamic part).
 template <class P>
-struct LbSmem {
+struct LbSmemRow {
     using T = typename P::T;
     using In = typename P::In;
     static constexpr int NW = kLbThreads / 32;
@@ -125,15 +109,25 @@ struct LbSmem {
     static constexpr size_t kQ0 = kDoff + sizeof(int32_t) * kLbCells;            // int[NT]
     static constexpr size_t kOff = kQ0 + sizeof(int32_t) * kLbThreads;            // int[NT + 1]
     static constexpr size_t kA = align_up(kOff + sizeof(int32_t) * (kLbThreads + 1), 16); // In[NT]
-    // unit region: per warp, the sorted keys and values of its unit; overlaid
-    // by the level-2 plan of a hot cell and by the giant-column scratch
-    static constexpr size_t kUnit = align_up(kA + sizeof(In) * kLbThreads, 16);
-    static constexpr size_t kStageK = kUnit;                                      // u32[NW][kLbUnit]
+    static constexpr size_t kStageK = align_up(kA + sizeof(In) * kLbThreads, 16); // u32[NW][kLbUnit]
     static constexpr size_t kStageV = kStageK + sizeof(uint32_t) * NW * kLbUnit;  // T[NW][kLbUnit]
+    static constexpr size_t kBytes = align_up(kStageV + sizeof(T) * NW * kLbUnit, 16);
+};
+
+// Shared memory of the work-list kernel (dynamic part); the staging slots
+// double as the giant-column scratch.
+template <class P>
+struct LbSmemHot {
+    using T = typename P::T;
+    static constexpr int NW = kLbThreads / 32;
+    static constexpr size_t kCnt = 0;                                             // int[kLbCells]
+    static constexpr size_t kNz = kCnt + sizeof(int32_t) * kLbCells;              // int[kLbCells]
+    static constexpr size_t kUl = kNz + sizeof(int32_t) * kLbCells;               // int[kLbCells + 1]
+    static constexpr size_t kStageK = align_up(kUl + sizeof(int32_t) * (kLbCells + 1), 16);
+    static constexpr size_t kStageV = kStageK + sizeof(uint32_t) * NW * kLbUnit;
+    static constexpr size_t kStageEnd = kStageV + sizeof(T) * NW * kLbUnit;
     static constexpr size_t kGiant = kLbBmBytes + (sizeof(T) + sizeof(int32_t)) * kLbThreads;
-    static constexpr size_t kUnitBytes = std::max(std::max((sizeof(uint32_t) + sizeof(T)) * NW * kLbUnit,
-                                                           sizeof(int32_t) * (2 * kLbCells + 2)), kGiant);
-    static constexpr size_t kBytes = align_up(kUnit + kUnitBytes, 16);
+    static constexpr size_t kBytes = align_up(kStageK + std::max(kStageEnd - kStageK, kGiant), 16);
 };
 
 __device__ __forceinline__ double lb_shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
@@ -252,16 +246,6 @@ struct LbOut {
     }
 };
 
-// The arrays and scalars of one row that the warp-level steps need.
-template <class P>
-struct LbRowArgs {
-    uint32_t *k1, *k2;
-    typename P::T *v1, *v2;
-    int lbits;
-    LbOut<P> out;
-    unsigned *err;
-};
-
 // Loads the descriptors of lists [t0, t0 + NT) of a row (B row start, and
 // the A value when `s_a` is given) and the exclusive prefix sums of their
 // lengths; returns the chunk's product count.  Callers synchronise before
@@ -306,7 +290,8 @@ __device__ __forceinline__ void lb_locate(const int32_t *s_off, const int32_t *s
 }
 
 // ---------------------------------------------------------------------------
-// Symbolic pass: distinct columns of each long row, by bitmap.
+// Distinct columns of each long row, by bitmap: the symbolic pass's row
+// lengths (P = PIdx), or the numeric pass's counts per cell (value P).
 // ---------------------------------------------------------------------------
 template <class P>
 __global__ void __launch_bounds__(kLsThreads, 1) k_long_sym(RowJob j) {
@@ -347,13 +332,33 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_long_sym(RowJob j) {
                 }
                 g.sync();
             }
-            int cnt = 0;
-            for (int i = threadIdx.x; i < words; i += kLsThreads) cnt += __popc(bm[i]);
-            int tot;
-            g.scan_excl(cnt, tot);
-            count += tot;
+            if constexpr (P::kVal) {
+                // the numeric pass's cells: 2^sh columns each, never across a window
+                uint16_t *cells = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(j.arena) +
+                                                               j.arena_off[r] + lb_layout<P>(j.slot_nprod[r]).cells);
+                const int sh = lb_shift(ncols);
+                const int d0 = (int)(w0 >> sh), nd = (int)(((int64_t)wn + (1 << sh) - 1) >> sh);
+                for (int d = threadIdx.x; d < nd; d += kLsThreads) {
+                    const uint32_t lo = (uint32_t)d << sh, hi = min(lo + (1u << sh), wn);
+                    int c = 0;
+                    for (uint32_t b = lo; b < hi;) {
+                        const uint32_t wi = b >> 5, sb = b & 31, nb = min(32u - sb, hi - b);
+                        const uint32_t msk = nb == 32 ? 0xffffffffu : (((1u << nb) - 1u) << sb);
+                        c += __popc(bm[wi] & msk);
+                        b += nb;
+                    }
+                    cells[d0 + d] = (uint16_t)c;
+                }
+            } else {
+                int cnt = 0;
+                for (int i = threadIdx.x; i < words; i += kLsThreads) cnt += __popc(bm[i]);
+                int tot;
+                g.scan_excl(cnt, tot);
+                count += tot;
+            }
+            g.sync();   // the bitmap is cleared for the next window
         }
-        if (threadIdx.x == 0 && j.out_cnt != nullptr) j.out_cnt[row] = count;
+        if (!P::kVal && threadIdx.x == 0 && j.out_cnt != nullptr) j.out_cnt[row] = count;
         g.sync();
     }
 }
@@ -489,190 +494,6 @@ __device__ __forceinline__ void lb_warp_sort(uint32_t (&k)[8], T (&v)[8], int la
     }
 }
 
-// Up to NW units at once, one per warp (`have`: this warp has a unit of m
-// <= kLbUnit products at gk/gv whose columns start at col_lo, inside one
-// aligned window of 2^16 columns).  The warps sort, count their distinct
-// columns, exchange the counts, then reduce every run and write it at its
-// place after obase.  Returns the group's output count (same in every thread).
-template <class P, int NT>
-__device__ __noinline__ int64_t lb_group(const BlockGrp<NT> &g, bool have, const uint32_t *gk, const typename P::T *gv, int m,
-                            int64_t col_lo, int lbits, const LbOut<P> &out, int64_t obase, unsigned char *smem) {
-    using T = typename P::T;
-    using L_ = LbSmem<P>;
-    constexpr int NW = NT / 32;
-    constexpr unsigned kFull = 0xffffffffu;
-    __shared__ int s_gcnt[NW];
-    __shared__ uint32_t s_stm[NW][kLbUnit / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L_::kStageK) + warp * kLbUnit;
-    T *sv = reinterpret_cast<T *>(smem + L_::kStageV) + warp * kLbUnit;
-    uint32_t k[8];
-    T v[8];
-    unsigned stf = 0;
-    int lbase = 0;
-    if (have) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int idx = i * 32 + lane;
-            k[i] = kLbPad;
-            v[i] = T();
-            if (idx < m) {
-                k[i] = __ldcs(gk + idx);
-                v[i] = gv[idx];
-            }
-        }
-        lb_warp_sort<T>(k, v, lane);
-        const uint32_t before = __shfl_up_sync(kFull, k[7], 1);
-        int nst = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t prv = i ? k[i - 1] : before;
-            if (k[i] != kLbPad && ((lane == 0 && i == 0) || (prv >> 16) != (k[i] >> 16))) {
-                stf |= 1u << i;
-                ++nst;
-            }
-        }
-        int x = nst;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(kFull, x, d);
-            if (lane >= d) x += y;
-        }
-        lbase = x - nst;
-        if (lane == 31) s_gcnt[warp] = x;
-    } else if (lane == 0) {
-        s_gcnt[warp] = 0;
-    }
-    g.sync();
-    int64_t wbase = 0, gtot = 0;
-#pragma unroll
-    for (int x = 0; x < NW; ++x) {
-        const int c = s_gcnt[x];
-        wbase += x < warp ? c : 0;
-        gtot += c;
-    }
-    if (have) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            sk[lane * 8 + i] = k[i];
-            sv[lane * 8 + i] = v[i];
-        }
-        // start bits of the sorted positions (bit p of word p / 32): four lanes per word
-        uint32_t word = stf << (8 * (lane & 3));
-        word |= __shfl_xor_sync(kFull, word, 1);
-        word |= __shfl_xor_sync(kFull, word, 2);
-        if ((lane & 3) == 0) s_stm[warp][lane >> 2] = word;
-        __syncwarp();
-        const uint32_t *stm = s_stm[warp];
-        const int64_t ob = obase + wbase;
-        const int64_t wc = col_lo - (col_lo & 0xffff);
-        unsigned longm = 0;
-        int r = lbase;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if ((stf >> i) & 1u) {
-                const int idx = lane * 8 + i, x = lb_next_start(stm, idx, m);
-                if (x - idx > kLbRunShort) {
-                    longm |= 1u << i;
-                } else {
-                    T s;
-                    if (x - idx == 1) s = sv[idx];
-                    else if (x - idx == 2) s = P::add(sv[idx], sv[idx + 1]);
-                    else s = lb_stack_reduce<P>(sk, sv, idx, x);
-                    out.put(ob + r, wc + (k[i] >> 16), s);
-                }
-                ++r;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            unsigned bm = __ballot_sync(kFull, (longm >> i) & 1u);
-            const int ri = lbase + __popc(stf & ((1u << i) - 1u));
-            while (bm) {
-                const int src = __ffs(bm) - 1;
-                bm &= bm - 1;
-                const int rb = src * 8 + i;
-                const int rr = __shfl_sync(kFull, ri, src);
-                const uint32_t col = __shfl_sync(kFull, k[i] >> 16, src);
-                const int re = lb_next_start(stm, rb, m);
-                const T s = lb_warp_run<P>(sk, sv, rb, re, lbits);
-                if (lane == 0) out.put(ob + rr, wc + col, s);
-            }
-        }
-    }
-    g.sync();
-    return gtot;
-}
-
-// A column of m > kLbUnit products (keys gk, values gv in device memory):
-// values go to their list's slot, present lists are marked in a bitmap, each
-// thread reduces an aligned range of lists with the stack and the threads'
-// results are combined as the tree levels above.  Writes one output.
-template <class P, int NT>
-__device__ __noinline__ void lb_giant(const BlockGrp<NT> &g, const uint32_t *gk, const typename P::T *gv, int m, int L, int lbits,
-                         typename P::T *slots, const LbOut<P> &out, int64_t w, int64_t col, unsigned char *smem) {
-    using T = typename P::T;
-    using L_ = LbSmem<P>;
-    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L_::kUnit);
-    T *pv = reinterpret_cast<T *>(smem + L_::kUnit + kLbBmBytes);
-    int32_t *pf = reinterpret_cast<int32_t *>(smem + L_::kUnit + kLbBmBytes + sizeof(T) * NT);
-    const int tid = (int)threadIdx.x;
-    const int words = (L + 31) >> 5;
-    for (int i = tid; i < words; i += NT) bm[i] = 0u;
-    g.sync();
-    for (int i = tid; i < m; i += NT) {
-        const uint32_t t = __ldcs(gk + i) & 0xffffu;
-        if ((int)t < L) {
-            slots[t] = gv[i];
-            atomicOr(&bm[t >> 5], 1u << (t & 31));
-        }
-    }
-    g.sync();   // slot writes are visible to the block after the barrier
-    constexpr int LOGNT = lb_bitlen(NT) - 1;
-    const int ss = lbits > LOGNT ? lbits - LOGNT : 0;
-    const int t0 = tid << ss, t1 = min((tid + 1) << ss, L);
-    T V[kLbDepth];
-    int G[kLbDepth];
-    int nv = 0, prev = 0;
-    for (int t = t0; t < t1; ++t) {
-        if (!((bm[t >> 5] >> (t & 31)) & 1u)) {
-            // skip the rest of an empty word quickly
-            if (((bm[t >> 5] >> (t & 31)) == 0u)) t |= 31;
-            continue;
-        }
-        if (nv > 0) {
-            const int d = 32 - __clz(prev ^ t);
-            while (nv > 1 && G[nv - 1] < d) {
-                V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
-                --nv;
-            }
-            G[nv] = d;
-        }
-        if (nv == kLbDepth) {
-            V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
-            --nv;
-        }
-        V[nv++] = slots[t];
-        prev = t;
-    }
-    while (nv > 1) {
-        V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
-        --nv;
-    }
-    pv[tid] = nv ? V[0] : T();
-    pf[tid] = nv ? 1 : 0;
-    g.sync();
-    for (int h = 1; h < NT; h <<= 1) {
-        if ((tid & (2 * h - 1)) == 0 && pf[tid + h]) {
-            pv[tid] = pf[tid] ? P::add(pv[tid], pv[tid + h]) : pv[tid + h];
-            pf[tid] = 1;
-        }
-        g.sync();
-    }
-    if (tid == 0) out.put(w, col, pv[0]);
-    g.sync();
-}
-
 // One unit of m <= kLbUnit products (keys gk, values gv in device memory)
 // whose columns start at col_lo, inside one aligned window of 2^16 columns,
 // by one warp: sorted in registers, every run of equal columns reduced in tree
@@ -765,227 +586,111 @@ __device__ __noinline__ void lb_wunit(const uint32_t *gk, const typename P::T *g
     __syncwarp();   // the staging slots are reused by the warp's next unit
 }
 
-// Records work for the block phase after the warps' units.
-__device__ __forceinline__ void lb_defer(LbDefer *dl, int *s_n, int64_t cap, int32_t kind, int st, int m, int64_t col,
-                                         int64_t ob, unsigned *err) {
-    if ((threadIdx.x & 31) == 0) {
-        const int i = atomicAdd(s_n, 1);
-        if (i < cap) dl[i] = LbDefer{kind, st, m, 0, col, ob};
-        else atomicOr(err, 1u);   // cannot happen: see lb_defer_cap
-    }
-    __syncwarp();
-}
-
-// A hot cell (m > kLbUnit products at [st0, st0 + m) of the level-1 arrays,
-// cw <= 256 columns from cell_lo) split by one warp: counted per column in
-// the warp's staging slots, cut into units like the cells of the row, copied
-// column by column to the same region of the level-2 arrays, then every unit
-// processed by the warp at its offset (ob plus the nonzero columns before
-// it); a column of more than kLbUnit products is deferred to the block.
-template <class P>
-__device__ __noinline__ void lb_whot(const LbRowArgs<P> &ra, int st0, int m, int64_t cell_lo, int cw, int64_t ob,
-                                     uint32_t *sk, typename P::T *sv, int32_t *wm, LbDefer *dl, int *s_nd,
-                                     int64_t dcap) {
-    constexpr unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    int32_t *cnt = reinterpret_cast<int32_t *>(sk);
-    const uint32_t *k1 = ra.k1 + st0;
-    const typename P::T *v1 = ra.v1 + st0;
-    uint32_t *k2 = ra.k2 + st0;
-    typename P::T *v2 = ra.v2 + st0;
-    int32_t *wend = wm, *wnz = wm + 256;
-    uint32_t *wcut = reinterpret_cast<uint32_t *>(wm + 512);
-    const uint32_t cmask = (uint32_t)cw - 1u;
-    for (int c = lane; c < 256; c += 32) cnt[c] = 0;
-    __syncwarp();
-    for (int i = lane; i < m; i += 32) atomicAdd(&cnt[(__ldcs(k1 + i) >> 16) & cmask], 1);
-    __syncwarp();
-    // lane l owns columns 8l .. 8l + 7
-    int c[8], sum = 0, nz = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        c[e] = cnt[lane * 8 + e];
-        sum += c[e];
-        nz += c[e] > 0 ? 1 : 0;
-    }
-    int xs = sum, xn = nz;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int ys = __shfl_up_sync(kFull, xs, d), yn = __shfl_up_sync(kFull, xn, d);
-        if (lane >= d) { xs += ys; xn += yn; }
-    }
-    int S = xs - sum, Z = xn - nz;
-    int prevc = __shfl_up_sync(kFull, c[7], 1);
-    if (lane == 0) prevc = 0;
-    unsigned flags = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int col = lane * 8 + e;
-        const int Sp = S - prevc;
-        if (col < cw && (col == 0 || c[e] > kLbHalf || prevc > kLbHalf || (S / kLbHalf) != (Sp / kLbHalf)))
-            flags |= 1u << e;
-        cnt[col] = S;
-        wnz[col] = Z;
-        Z += c[e] > 0 ? 1 : 0;
-        prevc = c[e];
-        S += c[e];
-    }
-    uint32_t word = flags << (8 * (lane & 3));
-    word |= __shfl_xor_sync(kFull, word, 1);
-    word |= __shfl_xor_sync(kFull, word, 2);
-    if ((lane & 3) == 0) wcut[lane >> 2] = word;
-    __syncwarp();
-    for (int i = lane; i < m; i += 32) {
-        const uint32_t key = __ldcs(k1 + i);
-        const int pos = atomicAdd(&cnt[(key >> 16) & cmask], 1);
-        k2[pos] = key;
-        v2[pos] = v1[i];
-    }
-    __syncwarp();
-    for (int col = lane; col < cw; col += 32) wend[col] = cnt[col];
-    __syncwarp();
-    // units: column ranges between consecutive cut marks
-    int c0 = 0;
-    while (c0 < cw) {
-        int c1 = c0 + 1;
-        while (c1 < cw && !((wcut[c1 >> 5] >> (c1 & 31)) & 1u)) ++c1;
-        const int st = c0 ? wend[c0 - 1] : 0, en = wend[c1 - 1];
-        if (en > st) {
-            const int64_t o2 = ob + wnz[c0];
-            if (en - st <= kLbUnit)
-                lb_wunit<P>(k2 + st, v2 + st, en - st, cell_lo + c0, ra.lbits, ra.out, o2, sk, sv);
-            else
-                lb_defer(dl, s_nd, dcap, kLbDeferGiant2, st0 + st, en - st, cell_lo + c0, o2, ra.err);
-        }
-        c0 = c1;
-    }
-}
-
-// What the levels of one row share (passed by value).
-template <class P>
-struct LbRow {
-    uint32_t *k1, *k2;
-    typename P::T *v1, *v2, *slots;
-    int32_t *meta;
-    int L, lbits, sh;
-    LbOut<P> out;
-};
-
-// The units of a level in column order: units of at most kLbUnit products
-// go to the warps, NW non-empty ones at a time (lb_group); a larger one is a
-// giant column (level 2, or level 1 with one-column cells) or a hot cell
-// (level 1), split by column.  Level 1 reads the units from the row's plan
-// in shared memory (cells ul[u] .. ul[u + 1], cell d ending at cnt[d]);
-// level 2 reads the plan of one hot cell from device memory (meta).  Returns
-// the output cursor after the level.
+// A column of m > kLbUnit products (keys gk, values gv in device memory):
+// values go to their list's slot, present lists are marked in a bitmap, each
+// thread reduces an aligned range of lists with the stack and the threads'
+// results are combined as the tree levels above.  Writes one output.
+// `slots` holds kLbSlots values of this block; `scratch` is shared memory of
+// at most kLbBmBytes + (sizeof(T) + 4) * NT bytes.
 template <class P, int NT>
-__device__ int64_t lb_hot(const BlockGrp<NT> &g, const LbRow<P> &rw, int st0, int m, int64_t cell_lo, int64_t w,
-                          unsigned char *smem);
-
-template <class P, int NT, int LEVEL>
-__device__ int64_t lb_level(const BlockGrp<NT> &g, const LbRow<P> &rw, int nu, const int32_t *ul, const int32_t *cnt,
-                            int base, int64_t cell_lo, int64_t w, unsigned char *smem) {
-    constexpr int NW = NT / 32;
-    const int warp = threadIdx.x >> 5;
-    const uint32_t *k = LEVEL == 1 ? rw.k1 : rw.k2;
-    const typename P::T *v = LEVEL == 1 ? rw.v1 : rw.v2;
-    int u = 0;
-    while (u < nu) {
-        int my_st = 0, my_en = 0, taken = 0;
-        int64_t my_cl = 0;
-        while (u < nu) {
-            const int c0 = ul[u], c1 = ul[u + 1];
-            const int st = base + (c0 ? cnt[c0 - 1] : 0), en = base + cnt[c1 - 1];
-            const int64_t cl = LEVEL == 1 ? (int64_t)c0 << rw.sh : cell_lo + c0;
-            if (en - st > kLbUnit) {
-                if (taken > 0) break;   // the group first
-                bool split = false;
-                if constexpr (LEVEL == 1) {
-                    if (rw.sh > 0) {
-                        w = lb_hot<P, NT>(g, rw, st, en - st, cl, w, smem);
-                        split = true;
-                    }
-                }
-                if (!split) {
-                    lb_giant<P, NT>(g, k + st, v + st, en - st, rw.L, rw.lbits, rw.slots, rw.out, w, cl, smem);
-                    ++w;
-                }
-                ++u;
-                continue;
-            }
-            if (taken == NW) break;
-            if (en > st) {
-                if (taken == warp) {
-                    my_st = st;
-                    my_en = en;
-                    my_cl = cl;
-                }
-                ++taken;
-            }
-            ++u;
-        }
-        if (taken > 0)
-            w += lb_group<P, NT>(g, warp < taken, k + my_st, v + my_st, my_en - my_st, my_cl, rw.lbits, rw.out, w,
-                                 smem);
-    }
-    return w;
-}
-
-// A cell of m > kLbUnit products at [st0, st0 + m) of the level-1 arrays:
-// counted per column, planned into units like the cells of the row, copied to
-// the same region of the level-2 arrays in column order, and processed as
-// level 2.  Returns the output cursor after the cell.
-template <class P, int NT>
-__device__ int64_t lb_hot(const BlockGrp<NT> &g, const LbRow<P> &rw, int st0, int m, int64_t cell_lo, int64_t w,
-                          unsigned char *smem) {
-    using L_ = LbSmem<P>;
-    int32_t *cnt2 = reinterpret_cast<int32_t *>(smem + L_::kUnit);
-    int32_t *ul2 = cnt2 + kLbCells;
-    const uint32_t *k1 = rw.k1 + st0;
-    const typename P::T *v1 = rw.v1 + st0;
-    uint32_t *k2 = rw.k2 + st0;
-    typename P::T *v2 = rw.v2 + st0;
-    const int cw = 1 << rw.sh;
+__device__ __noinline__ void lb_giant(const BlockGrp<NT> &g, const uint32_t *gk, const typename P::T *gv, int m,
+                                      int L, int lbits, typename P::T *slots, const LbOut<P> &out, int64_t w,
+                                      int64_t col, unsigned char *scratch) {
+    using T = typename P::T;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(scratch);
+    T *pv = reinterpret_cast<T *>(scratch + kLbBmBytes);
+    int32_t *pf = reinterpret_cast<int32_t *>(scratch + kLbBmBytes + sizeof(T) * NT);
     const int tid = (int)threadIdx.x;
-    for (int i = tid; i < cw; i += NT) cnt2[i] = 0;
+    const int words = (L + 31) >> 5;
+    for (int i = tid; i < words; i += NT) bm[i] = 0u;
     g.sync();
-    for (int i = tid; i < m; i += NT) atomicAdd(&cnt2[(k1[i] >> 16) & (uint32_t)(cw - 1)], 1);
-    g.sync();
-    const int nu2 = lb_plan<NT>(g, cnt2, cw, ul2, 0);
     for (int i = tid; i < m; i += NT) {
-        const uint32_t key = k1[i];
-        const int pos = atomicAdd(&cnt2[(key >> 16) & (uint32_t)(cw - 1)], 1);
-        k2[pos] = key;
-        v2[pos] = v1[i];
+        const uint32_t t = __ldcs(gk + i) & 0xffffu;
+        if ((int)t < L) {
+            slots[t] = gv[i];
+            atomicOr(&bm[t >> 5], 1u << (t & 31));
+        }
     }
+    g.sync();   // slot writes are visible to the block after the barrier
+    constexpr int LOGNT = lb_bitlen(NT) - 1;
+    const int ss = lbits > LOGNT ? lbits - LOGNT : 0;
+    const int t0 = tid << ss, t1 = min((tid + 1) << ss, L);
+    T V[kLbDepth];
+    int G[kLbDepth];
+    int nv = 0, prev = 0;
+    for (int t = t0; t < t1; ++t) {
+        if (!((bm[t >> 5] >> (t & 31)) & 1u)) {
+            // skip the rest of an empty word quickly
+            if (((bm[t >> 5] >> (t & 31)) == 0u)) t |= 31;
+            continue;
+        }
+        if (nv > 0) {
+            const int d = 32 - __clz(prev ^ t);
+            while (nv > 1 && G[nv - 1] < d) {
+                V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+                --nv;
+            }
+            G[nv] = d;
+        }
+        if (nv == kLbDepth) {
+            V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+            --nv;
+        }
+        V[nv++] = slots[t];
+        prev = t;
+    }
+    while (nv > 1) {
+        V[nv - 2] = P::add(V[nv - 2], V[nv - 1]);
+        --nv;
+    }
+    pv[tid] = nv ? V[0] : T();
+    pf[tid] = nv ? 1 : 0;
     g.sync();
-    // the plan moves to device memory: the units reuse shared memory
-    for (int i = tid; i < cw; i += NT) rw.meta[i] = cnt2[i];
-    for (int i = tid; i <= nu2; i += NT) rw.meta[kLbCells + i] = ul2[i];
+    for (int h = 1; h < NT; h <<= 1) {
+        if ((tid & (2 * h - 1)) == 0 && pf[tid + h]) {
+            pv[tid] = pf[tid] ? P::add(pv[tid], pv[tid + h]) : pv[tid + h];
+            pf[tid] = 1;
+        }
+        g.sync();
+    }
+    if (tid == 0) out.put(w, col, pv[0]);
     g.sync();
-    return lb_level<P, NT, 2>(g, rw, nu2, rw.meta + kLbCells, rw.meta, st0, cell_lo, w, smem);
 }
+
+// One record of the work list: a hot cell, or a giant column of a row whose
+// cells are single columns, at [st, st + m) of the row's level-1 arrays.
+struct LbWork {
+    int32_t slot, kind, st, m;
+    int64_t col, ob;
+};
+constexpr int32_t kLbWorkHot = 0, kLbWorkGiant = 1;
+
+static_assert(sizeof(LbWork) == kLbWorkBytes, "work-list record size");
 
 template <class P>
 __global__ void __launch_bounds__(kLbThreads, 2) k_long_bucket(RowJob j) {
     using T = typename P::T;
     using In = typename P::In;
-    using L_ = LbSmem<P>;
+    using L_ = LbSmemRow<P>;
     constexpr int NT = kLbThreads;
+    constexpr int NW = NT / 32;
     constexpr int KH = 8;   // products per thread per step: histogram
     constexpr int KS = 4;   // ... scatter
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ws[NT / 32 + 1];
+    __shared__ int s_next;
     BlockGrp<NT> g;
     g.ws = ws;
     int32_t *cnt = reinterpret_cast<int32_t *>(smem + L_::kCnt);
     int32_t *ul = reinterpret_cast<int32_t *>(smem + L_::kUl);
+    int32_t *doff = reinterpret_cast<int32_t *>(smem + L_::kDoff);
     int32_t *s_q0 = reinterpret_cast<int32_t *>(smem + L_::kQ0);
     int32_t *s_off = reinterpret_cast<int32_t *>(smem + L_::kOff);
     In *s_a = reinterpret_cast<In *>(smem + L_::kA);
-    int32_t *doff = reinterpret_cast<int32_t *>(smem + L_::kDoff);
-    constexpr int NW = NT / 32;
-    __shared__ int s_next, s_nd;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L_::kStageK) + warp * kLbUnit;
+    T *sv = reinterpret_cast<T *>(smem + L_::kStageV) + warp * kLbUnit;
+    LbWork *work = static_cast<LbWork *>(j.lb_work);
     const int64_t ncols = j.bcols;
     const int sh = lb_shift(ncols);
     const int ncell = (int)(((ncols > 0 ? ncols - 1 : 0) >> sh) + 1);
@@ -997,22 +702,14 @@ __global__ void __launch_bounds__(kLbThreads, 2) k_long_bucket(RowJob j) {
         const int64_t n = j.slot_nprod[r];
         const int lbits = L > 1 ? lb_bitlen((uint64_t)(L - 1)) : 0;
         unsigned char *ap = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[r];
-        const LbLayout lay = lb_layout<P>(n, L);
+        const LbLayout lay = lb_layout<P>(n);
+        uint32_t *k1 = reinterpret_cast<uint32_t *>(ap + lay.k1);
+        T *v1 = reinterpret_cast<T *>(ap + lay.v1);
+        const uint16_t *cells = reinterpret_cast<const uint16_t *>(ap + lay.cells);
         const int64_t obeg = j.out_rp[row];
-        LbRow<P> rw;
-        rw.k1 = reinterpret_cast<uint32_t *>(ap + lay.k1);
-        rw.v1 = reinterpret_cast<T *>(ap + lay.v1);
-        rw.k2 = reinterpret_cast<uint32_t *>(ap + lay.k2);
-        rw.v2 = reinterpret_cast<T *>(ap + lay.v2);
-        rw.slots = reinterpret_cast<T *>(ap + lay.slots);
-        rw.meta = reinterpret_cast<int32_t *>(ap + lay.meta);
-        rw.L = L;
-        rw.lbits = lbits;
-        rw.sh = sh;
-        rw.out = LbOut<P>{j.out_col + obeg, static_cast<typename P::Out *>(j.out_val) + obeg, j.out_rp[row + 1] - obeg};
-        uint32_t *k1 = rw.k1;
-        T *v1 = rw.v1;
-        // 1. histogram of the row's products over the cells
+        const LbOut<P> out{j.out_col + obeg, static_cast<typename P::Out *>(j.out_val) + obeg,
+                           j.out_rp[row + 1] - obeg};
+        // a. histogram of the row's products over the cells
         for (int d = threadIdx.x; d < kLbCells; d += NT) cnt[d] = 0;
         g.sync();
         for (int t0 = 0; t0 < L; t0 += NT) {
@@ -1037,9 +734,9 @@ __global__ void __launch_bounds__(kLbThreads, 2) k_long_bucket(RowJob j) {
             }
             g.sync();
         }
-        // 2. units
+        // b. units
         const int nu = lb_plan<NT>(g, cnt, ncell, ul, win);
-        // 3. scatter the products to their cells' regions
+        // c. scatter the products to their cells' regions
         for (int t0 = 0; t0 < L; t0 += NT) {
             const int nc = min(NT, L - t0);
             const int tot = lb_load_chunk<In, NT>(g, ri, t0, s_q0, s_off, s_a);
@@ -1073,48 +770,16 @@ __global__ void __launch_bounds__(kLbThreads, 2) k_long_bucket(RowJob j) {
             }
             g.sync();
         }
-        // 4. distinct columns of every cell (one warp per cell, a bitmap of the
-        //    cell's columns in the warp's staging slots); cell d ends at cnt[d]
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L_::kStageK) + warp * kLbUnit;
-        T *sv = reinterpret_cast<T *>(smem + L_::kStageV) + warp * kLbUnit;
-        {
-            const int cw = 1 << sh, words = (cw + 31) >> 5;
-            for (int d = warp; d < ncell; d += NW) {
-                const int st = d ? cnt[d - 1] : 0, m = cnt[d] - st;
-                if (m <= 1) {
-                    if (lane == 0) doff[d] = m;
-                    continue;
-                }
-                for (int i = lane; i < words; i += 32) sk[i] = 0u;
-                __syncwarp();
-                for (int i = lane; i < m; i += 32) {
-                    const uint32_t c = (k1[st + i] >> 16) & (uint32_t)(cw - 1);
-                    atomicOr(&sk[c >> 5], 1u << (c & 31));
-                }
-                __syncwarp();
-                int x = 0;
-                for (int i = lane; i < words; i += 32) x += __popc(sk[i]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) doff[d] = x;
-                __syncwarp();
-            }
-        }
-        if (threadIdx.x == 0) {
-            s_next = 0;
-            s_nd = 0;
-        }
-        g.sync();
-        // 5. output offsets of the cells
-        int64_t w;
+        // d. the cells' places in the output, from their distinct-column
+        //    counts; cell d now ends at cnt[d]
+        int64_t len;
         {
             constexpr int PER = kLbCells / NT;
             int c[PER], sum = 0;
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
                 const int d = threadIdx.x * PER + e;
-                c[e] = d < ncell ? doff[d] : 0;
+                c[e] = d < ncell ? cells[d] : 0;
                 sum += c[e];
             }
             int tot;
@@ -1125,67 +790,192 @@ __global__ void __launch_bounds__(kLbThreads, 2) k_long_bucket(RowJob j) {
                 if (d < ncell) doff[d] = ex;
                 ex += c[e];
             }
-            w = tot;
+            len = tot;
         }
+        if (threadIdx.x == 0) s_next = 0;
         g.sync();
-        // 6. the units, taken by the warps one at a time
-        const int64_t dcap = lb_defer_cap(n);
-        LbDefer *dl = reinterpret_cast<LbDefer *>(ap + lay.defer);
-        LbRowArgs<P> ra{rw.k1, rw.k2, rw.v1, rw.v2, lbits, rw.out, j.err};
-        int32_t *wm = reinterpret_cast<int32_t *>(ap + lay.wmeta) + warp * kLbWmeta;
+        // e. the units, taken by the warps one at a time
         for (;;) {
             int u = 0;
             if (lane == 0) u = atomicAdd(&s_next, 1);
             u = __shfl_sync(0xffffffffu, u, 0);
             if (u >= nu) break;
             const int d0 = ul[u], d1 = ul[u + 1];
-            const int st = d0 ? cnt[d0 - 1] : 0, en = cnt[d1 - 1], m = en - st;
+            const int st = d0 ? cnt[d0 - 1] : 0, m = cnt[d1 - 1] - st;
             if (m == 0) continue;
             const int64_t ob = doff[d0], cl = (int64_t)d0 << sh;
-            if (m <= kLbUnit) lb_wunit<P>(k1 + st, v1 + st, m, cl, lbits, rw.out, ob, sk, sv);
-            else if (sh == 0) lb_defer(dl, &s_nd, dcap, kLbDeferGiant1, st, m, cl, ob, j.err);
-            else if (sh <= 8) lb_whot<P>(ra, st, m, cl, 1 << sh, ob, sk, sv, wm, dl, &s_nd, dcap);
-            else lb_defer(dl, &s_nd, dcap, kLbDeferHot, st, m, cl, ob, j.err);
-        }
-        g.sync();
-        // 7. the deferred work, by the whole block: hot cells of more than 256
-        //    columns (split and processed as level 2), then giant columns
-        const int nd = min(s_nd, (int)dcap);
-        for (int i = 0; i < nd; ++i) {
-            const LbDefer e = dl[i];
-            if (e.kind == kLbDeferHot) lb_hot<P, NT>(g, rw, e.st, e.m, e.col, e.ob, smem);
-        }
-        for (int i = 0; i < nd; ++i) {
-            const LbDefer e = dl[i];
-            if (e.kind == kLbDeferHot) continue;
-            const uint32_t *gk = e.kind == kLbDeferGiant1 ? rw.k1 : rw.k2;
-            const T *gv = e.kind == kLbDeferGiant1 ? rw.v1 : rw.v2;
-            lb_giant<P, NT>(g, gk + e.st, gv + e.st, e.m, L, lbits, rw.slots, rw.out, e.ob, e.col, smem);
+            if (m <= kLbUnit) {
+                lb_wunit<P>(k1 + st, v1 + st, m, cl, lbits, out, ob, sk, sv);
+            } else if (lane == 0) {
+                const int i = atomicAdd(j.lb_ctr, 1);
+                if (i < j.lb_cap) work[i] = LbWork{r, sh == 0 ? kLbWorkGiant : kLbWorkHot, st, m, cl, ob};
+                else atomicOr(j.err, 1u);   // cannot happen: see lb_work_cap
+            }
         }
         if (threadIdx.x == 0) {
-            if (w > rw.out.cap || (j.exact && w != rw.out.cap)) atomicOr(j.err, 1u);
-            if (j.out_cnt != nullptr) j.out_cnt[row] = w;
+            if (len > out.cap || (j.exact && len != out.cap)) atomicOr(j.err, 1u);
+            if (j.out_cnt != nullptr) j.out_cnt[row] = len;
         }
         g.sync();
     }
 }
 
+// The work list of a batch (hot cells and giant columns of its rows), taken
+// by persistent blocks one record at a time.
+template <class P>
+__global__ void __launch_bounds__(kLbThreads, 2) k_long_hot(RowJob j) {
+    using T = typename P::T;
+    using In = typename P::In;
+    using L_ = LbSmemHot<P>;
+    constexpr int NT = kLbThreads;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int ws[NT / 32 + 1];
+    __shared__ int s_item, s_next;
+    BlockGrp<NT> g;
+    g.ws = ws;
+    int32_t *cnt = reinterpret_cast<int32_t *>(smem + L_::kCnt);
+    int32_t *nzp = reinterpret_cast<int32_t *>(smem + L_::kNz);
+    int32_t *ul = reinterpret_cast<int32_t *>(smem + L_::kUl);
+    unsigned char *scratch = smem + L_::kStageK;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L_::kStageK) + warp * kLbUnit;
+    T *sv = reinterpret_cast<T *>(smem + L_::kStageV) + warp * kLbUnit;
+    const LbWork *work = static_cast<const LbWork *>(j.lb_work);
+    T *slots = static_cast<T *>(j.lb_slots) + (size_t)blockIdx.x * kLbSlots;
+    const int sh = lb_shift(j.bcols);
+    const int cw = 1 << sh;
+    const uint32_t cmask = (uint32_t)cw - 1u;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(j.lb_ctr + 1, 1);
+        g.sync();
+        const int i = s_item;
+        const int count = min(*(volatile int32_t *)j.lb_ctr, (int)j.lb_cap);
+        if (i >= count) break;
+        const LbWork wk = work[i];
+        const int row = j.rows[wk.slot];
+        const int L = row_in<In>(j, row).L;
+        const int lbits = L > 1 ? lb_bitlen((uint64_t)(L - 1)) : 0;
+        unsigned char *ap = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[wk.slot];
+        const LbLayout lay = lb_layout<P>(j.slot_nprod[wk.slot]);
+        const uint32_t *k1 = reinterpret_cast<const uint32_t *>(ap + lay.k1) + wk.st;
+        const T *v1 = reinterpret_cast<const T *>(ap + lay.v1) + wk.st;
+        uint32_t *k2 = reinterpret_cast<uint32_t *>(ap + lay.k2) + wk.st;
+        T *v2 = reinterpret_cast<T *>(ap + lay.v2) + wk.st;
+        const int64_t obeg = j.out_rp[row];
+        const LbOut<P> out{j.out_col + obeg, static_cast<typename P::Out *>(j.out_val) + obeg,
+                           j.out_rp[row + 1] - obeg};
+        const int m = wk.m;
+        if (wk.kind == kLbWorkGiant) {
+            lb_giant<P, NT>(g, k1, v1, m, L, lbits, slots, out, wk.ob, wk.col, scratch);
+            continue;
+        }
+        // a hot cell: products per column (one atomic per column and warp)
+        for (int c = threadIdx.x; c < cw; c += NT) cnt[c] = 0;
+        g.sync();
+        for (int b = warp * 32; b < m; b += NT) {
+            const int x = b + lane;
+            const uint32_t c = x < m ? ((__ldcs(k1 + x) >> 16) & cmask) : 0xffffffffu;
+            const unsigned same = __match_any_sync(kFull, c);
+            if (x < m && lane == __ffs(same) - 1) atomicAdd(&cnt[c], __popc(same));
+        }
+        g.sync();
+        const int nu = lb_plan<NT>(g, cnt, cw, ul, 0);
+        // nonzero columns before each column: its place among the cell's outputs
+        {
+            constexpr int PER = kLbCells / NT;
+            int f[PER], sum = 0;
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const int c = threadIdx.x * PER + e;
+                f[e] = c < cw && (c + 1 < cw ? cnt[c + 1] : m) > cnt[c] ? 1 : 0;
+                sum += f[e];
+            }
+            int tot;
+            int ex = g.scan_excl(sum, tot);
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const int c = threadIdx.x * PER + e;
+                if (c < cw) nzp[c] = ex;
+                ex += f[e];
+            }
+        }
+        g.sync();
+        for (int b = warp * 32; b < m; b += NT) {
+            const int x = b + lane;
+            uint32_t key = 0;
+            T val = T();
+            if (x < m) {
+                key = __ldcs(k1 + x);
+                val = v1[x];
+            }
+            const uint32_t c = x < m ? ((key >> 16) & cmask) : 0xffffffffu;
+            const unsigned same = __match_any_sync(kFull, c);
+            const int leader = __ffs(same) - 1;
+            int base = 0;
+            if (x < m && lane == leader) base = atomicAdd(&cnt[c], __popc(same));
+            base = __shfl_sync(kFull, base, leader);
+            if (x < m) {
+                const int pos = base + __popc(same & ((1u << lane) - 1u));
+                k2[pos] = key;
+                v2[pos] = val;
+            }
+        }
+        if (threadIdx.x == 0) s_next = 0;
+        g.sync();
+        // the cell's units, taken by the warps; column c now ends at cnt[c]
+        for (;;) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(&s_next, 1);
+            u = __shfl_sync(kFull, u, 0);
+            if (u >= nu) break;
+            const int c0 = ul[u], c1 = ul[u + 1];
+            const int st = c0 ? cnt[c0 - 1] : 0, m2 = cnt[c1 - 1] - st;
+            if (m2 == 0 || m2 > kLbUnit) continue;
+            lb_wunit<P>(k2 + st, v2 + st, m2, wk.col + c0, lbits, out, wk.ob + nzp[c0], sk, sv);
+        }
+        g.sync();
+        // its giant columns, by the block
+        for (int u = 0; u < nu; ++u) {
+            const int c0 = ul[u], c1 = ul[u + 1];
+            const int st = c0 ? cnt[c0 - 1] : 0, m2 = cnt[c1 - 1] - st;
+            if (m2 > kLbUnit) lb_giant<P, NT>(g, k2 + st, v2 + st, m2, L, lbits, slots, out, wk.ob + nzp[c0], wk.col + c0,
+                                             scratch);
+        }
+        g.sync();
+    }
+}
+
+// Blocks of the work-list kernel (persistent; each owns kLbSlots slots).
+inline int lb_hot_blocks() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return kLbHotPerSm * (sms > 0 ? sms : 1);
+}
+
 template <class P>
 cudaError_t launch_long_bucket(const RowJob &j, cudaStream_t st) {
+    cudaError_t e;
+    const size_t smb = (size_t)kLsWinBits / 8;
+    auto ks = k_long_sym<P>;
+    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb)) != cudaSuccess) return e;
     if constexpr (P::kVal) {
-        const size_t sm = LbSmem<P>::kBytes;
-        auto kern = k_long_bucket<P>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        kern<<<j.count, kLbThreads, sm, st>>>(j);
+        if ((e = cudaMemsetAsync(j.lb_ctr, 0, 2 * sizeof(int32_t), st)) != cudaSuccess) return e;
+        ks<<<j.count, kLsThreads, smb, st>>>(j);
+        auto kr = k_long_bucket<P>;
+        if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LbSmemRow<P>::kBytes)))
+            return e;
+        kr<<<j.count, kLbThreads, LbSmemRow<P>::kBytes, st>>>(j);
+        auto kh = k_long_hot<P>;
+        if ((e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LbSmemHot<P>::kBytes)))
+            return e;
+        kh<<<lb_hot_blocks(), kLbThreads, LbSmemHot<P>::kBytes, st>>>(j);
+        g_launches.fetch_add(3, std::memory_order_relaxed);
     } else {
-        const size_t sm = (size_t)kLsWinBits / 8;
-        auto kern = k_long_sym<P>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        kern<<<j.count, kLsThreads, sm, st>>>(j);
+        ks<<<j.count, kLsThreads, smb, st>>>(j);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
     }
-    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 

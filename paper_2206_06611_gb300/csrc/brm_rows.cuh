@@ -181,7 +181,7 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
 // none) or the merge rounds.
 template <class P>
 size_t long_bytes_t(int64_t n, int64_t L, bool bucket) {
-    if (bucket) return P::kVal ? lb_layout<P>(n, L).total : 256;
+    if (bucket) return P::kVal ? lb_layout<P>(n).total : 256;
     return long_row_bytes<P>(n, L);
 }
 
