@@ -339,6 +339,8 @@ def run_profile(args):
     """A short fixed sequence of calls for ncu to capture (no timing):
     er       two BRMerge-Precise calls on the ER workload (n = --profile-n);
     rmat     two BRMerge-Precise calls on R-MAT of scale --scale;
+             er and rmat take the long rows' numeric pass by column buckets
+             with --long-bucket;
     batched  a prepared batch of the 512-product mix, its numeric pass twice,
              then one brm_spgemm_batched call;
     diff     the differentiable workload's forward and backward once each."""
@@ -369,10 +371,10 @@ def run_profile(args):
         A = I.rmat(args.scale, 16) if args.workload == "rmat" else I.erdos_renyi(args.profile_n, 16)
         dA = brm.to_device(A, device="cuda:0")
         for _ in range(2):
-            C = brm.brm_spgemm_precise(dA, dA)
+            C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket)
             torch.cuda.synchronize()
             del C
-        info = {"profile": args.workload, "n": A.rows}
+        info = {"profile": args.workload, "n": A.rows, "long_bucket": args.long_bucket}
     info["launches"] = brm.brm_kernel_launches()
     print(json.dumps(info), flush=True)
 
@@ -459,6 +461,24 @@ def run_rmat(args):
                                                "rows": int(len(rows))}}
         del dA
         torch.cuda.empty_cache()
+    # the long rows' numeric pass by column buckets instead of merge rounds
+    # (option long_bucket; the same bits), FP64
+    dA = brm.to_device(A)
+
+    def bucket_step():
+        Cx = brm.brm_spgemm_precise(dA, dA, long_bucket=True)
+        del Cx
+
+    brm.brm_trace_reset()
+    brm.brm_trace_enable(True)
+    ms = _timed(bucket_step, args.steps, max(1, min(args.warmup, 2)))
+    t = brm.brm_trace_read()
+    brm.brm_trace_enable(False)
+    n_calls = args.steps + max(1, min(args.warmup, 2))
+    out["f64_long_bucket"] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9,
+                              "phases_ms": {k: round(v[0] / n_calls, 3) for k, v in t.items() if v[1]}}
+    del dA
+    torch.cuda.empty_cache()
     # BRMerge-Upper: C_bar of every product (about 251 GB here) does not fit
     # beside C, so it runs in row chunks
     dA = brm.to_device(A)
@@ -595,6 +615,8 @@ def main():
     ap.add_argument("--workload", default="er", choices=["er", "rmat", "batched", "diff"],
                     help="er: the headline line; the others print their own JSON line")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of --workload rmat")
+    ap.add_argument("--long-bucket", action="store_true",
+                    help="--profile: long rows' numeric pass by column buckets (option long_bucket)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -6,11 +6,11 @@ with option long_bucket, by column buckets: the row's products are scattered
 to column cells and every column is reduced in the merge tree's order.  Both
 numeric kernels must give the same bits as each other and as the oracle's
 Algorithm 1.
-The cases reach every branch of the numeric kernel: units of several cells,
-sub-ranges sorted by a thread and by a warp, runs reduced by a thread and by a
-warp, cells of more than 256 products split again by column, and columns of
-more than 256 products reduced over one slot per list; also B wider than one
-bitmap window and rows beyond the 65535-list limit (merge rounds).
+The cases reach every branch of the bucket kernels: units of several cells,
+runs reduced by one lane and by a whole warp, cells of more than 256 products
+split again by column (the work list), and columns of more than 256 products
+reduced over one slot per list, at both levels; also B wider than one bitmap
+window and rows beyond the 65535-list limit (merge rounds).
 """
 import numpy as np
 import pytest
