@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
 
 // The same numeric pass from a recorded order without staging the products:
 // every run start reads its products straight from B (list index by a search
-// in the list ends, B position, column and value), eight output positions
+// in the list ends, B position, column and value), four output positions
 // at a time so that their loads are in flight together.  Only the list
 // descriptors use shared memory, so many more warps fit an SM; used for the
 // rows of 32-key bins, whose staged form is limited by shared memory.
@@ -739,13 +739,17 @@ __device__ __noinline__ typename P::T perm_tree_reduce_direct(const uint16_t *pr
 }
 
 template <class P, int TPR, int E>
-__global__ void __launch_bounds__(256) k_rows_perm_direct(RowJob j) {
+__global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
     using Cf = RegCfg<TPR, E>;
     using In = typename P::In;
     using T = typename P::T;
     using Out = typename P::Out;
     constexpr unsigned kFull = 0xffffffffu;
-    constexpr int NB = 8;   // output positions whose loads are issued together
+    // output positions whose loads are issued together: four, so that the
+    // kernel fits 64 registers and four blocks of 8 warps an SM (eight
+    // positions took 98 registers and two blocks; the batched mix's numeric
+    // pass went from 49.2 to 44.9 ms)
+    constexpr int NB = 4;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int rho = lane / TPR, t = lane % TPR, rowbase = rho * TPR;
