@@ -98,12 +98,15 @@ __device__ __forceinline__ void cmpswap(uint32_t &a, uint32_t &b) {
 // Each merge stage k starts with a "flip" (position x against x ^ (k - 1)) and
 // continues with half cleaners (x against x ^ j), the smaller key always to
 // the lower position.
+// With `presorted`, every thread's E keys are already ascending, so the
+// stages of sizes k <= E (all inside a thread's registers) are skipped.
 template <int TPR, int E>
-__device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[E], int t) {
+__device__ __forceinline__ void reg_bitonic_sort(uint32_t (&key)[E], int t, bool presorted = false) {
     constexpr int CAP = E * TPR, LE = ilog2_c(E);
     constexpr unsigned kFull = 0xffffffffu;
 #pragma unroll
     for (int k = 2; k <= CAP; k <<= 1) {
+        if (k <= E && presorted) continue;
         if (k <= E) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
         const int L = has_row ? ri.L : 0;
 
         // ---- list descriptors: start of B_k*, A_ik, and the list ends ------
-        int carry = 0;
+        int carry = 0, maxlen = 0;
         for (int c0 = 0; __any_sync(kFull, c0 < L); c0 += TPR) {
             const int l = c0 + t;
             int len = 0;
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
                 d_q0[l] = q0;
                 if constexpr (P::kVal) d_a[l] = ri.aval[l];
             }
+            maxlen = max(maxlen, len);
             int incl = len;
 #pragma unroll
             for (int d = 1; d < TPR; d <<= 1) {
@@ -245,13 +249,53 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
         }
         if (t == 0) d_off[0] = 0;
         const int N = carry;
+#pragma unroll
+        for (int d = TPR / 2; d > 0; d >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, d, TPR));
+        // every list of every row of the warp fits one thread: thread t then
+        // holds list t, whose keys ascend, and the sort skips its first stages
+        const bool presorted = __all_sync(kFull, !has_row || (L <= TPR && maxlen <= E));
         __syncwarp();
 
-        // ---- multiplying phase: position p = i * TPR + t ---------------------
+        // ---- multiplying phase -----------------------------------------------
         uint32_t key[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) key[i] = kKeyPad;
-        {
+        if (presorted) {
+            // thread t: the products of list t in order, positions d_off[t] + i
+            const bool mine = has_row && t < L;
+            const int len = mine ? d_off[t + 1] - d_off[t] : 0;
+            const int q0 = mine ? d_q0[t] : 0, p0 = mine ? d_off[t] : 0;
+            In a = In();
+            if constexpr (P::kVal) {
+                if (mine) a = d_a[t];
+            }
+#pragma unroll
+            for (int i0 = 0; i0 < E; i0 += kRegU) {
+                int32_t c[kRegU];
+                In v[kRegU];
+#pragma unroll
+                for (int u = 0; u < kRegU; ++u) {
+                    c[u] = 0;
+                    v[u] = In();
+                    if (i0 + u < len) {
+                        c[u] = ld_keep(ri.bcol + q0 + i0 + u, keep);
+                        if constexpr (P::kVal) v[u] = ld_keep(ri.bval + q0 + i0 + u, keep);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRegU; ++u) {
+                    const int p = p0 + i0 + u;
+                    if (i0 + u < len) {
+                        key[i0 + u] = ((uint32_t)c[u] << SB) | (SB > 0 ? (uint32_t)p : 0u);
+                        if constexpr (P::kVal) {
+                            vals[p] = P::mul(a, v[u]);
+                            lidx[p] = (uint16_t)t;
+                        }
+                    }
+                }
+            }
+        } else {
+            // position p = i * TPR + t
             int l = 0;
 #pragma unroll
             for (int i0 = 0; i0 < E; i0 += kRegU) {
@@ -295,7 +339,7 @@ __global__ void __launch_bounds__(256) k_rows_reg(RowJob j) {
         }
 
         // ---- accumulating phase: sort, then runs of equal columns -----------
-        reg_bitonic_sort<TPR, E>(key, t);
+        reg_bitonic_sort<TPR, E>(key, t, presorted);
 
         if constexpr (P::kPerm) {
             // symbolic, recording the order: thread t holds sorted positions
