@@ -176,15 +176,6 @@ __device__ __noinline__ typename P::T lb_stack_reduce(uint32_t *ks, typename P::
     return top;
 }
 
-// First index in [lo, hi) whose key's column part exceeds `col`.
-__device__ __forceinline__ int lb_run_end(const uint32_t *ks, int lo, int hi, uint32_t col) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((ks[mid] >> 16) <= col) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 // End of the run starting at sorted position idx of a unit of m products:
 // the next set bit of the unit's 256-bit run-start mask, else m.
 __device__ __forceinline__ int lb_next_start(const uint32_t *stm, int idx, int m) {
