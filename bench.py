@@ -341,14 +341,15 @@ def run_profile(args):
     rmat     two BRMerge-Precise calls on R-MAT of scale --scale;
              er and rmat take the long rows' numeric pass by column buckets
              with --long-bucket;
-    batched  a prepared batch of the 512-product mix, its numeric pass twice,
-             then one brm_spgemm_batched call;
+    batched  a prepared batch of the product mix (--batch-count products,
+             512 by default), its numeric pass twice, then one
+             brm_spgemm_batched call;
     diff     the differentiable workload's forward and backward once each."""
     import torch
     from paper_2206_06611_gb300 import brm
     torch.cuda.set_device(0)
     if args.workload == "batched":
-        mats = I.batched_mix(512)
+        mats = I.batched_mix(args.batch_count)
         dev = [brm.to_device(M) for M in mats]
         b = brm.Batch(dev, dev)
         for _ in range(2):
@@ -615,6 +616,8 @@ def main():
     ap.add_argument("--workload", default="er", choices=["er", "rmat", "batched", "diff"],
                     help="er: the headline line; the others print their own JSON line")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of --workload rmat")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="--profile --workload batched: products of the mix (the first of the 512)")
     ap.add_argument("--long-bucket", action="store_true",
                     help="--profile: long rows' numeric pass by column buckets (option long_bucket)")
     args = ap.parse_args()

@@ -844,13 +844,25 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
         const unsigned gmask = (TPR == 32) ? kFull : (((1u << TPR) - 1u) << rowbase);
         const unsigned lt = (1u << lane) - 1u;
         int count = 0;
+        // the recorded entries of the next batch are loaded while this one is
+        // processed
+        uint32_t en[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int pos = b * TPR + t;
+            en[b] = pos < N ? __ldcs(pr + pos) : 0u;
+        }
         for (int j0 = 0; __any_sync(kFull, j0 * TPR < N); j0 += NB) {
             uint32_t e[NB];
             int q[NB], l[NB];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const int pos = (j0 + b) * TPR + t;
-                e[b] = pos < N ? __ldcs(pr + pos) : 0u;
+                e[b] = en[b];
+                const int pos = (j0 + NB + b) * TPR + t;
+                en[b] = pos < N ? __ldcs(pr + pos) : 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
                 l[b] = 0;
                 q[b] = 0;
                 if (e[b] & kPermStart) {
