@@ -742,15 +742,16 @@ __global__ void __launch_bounds__(256) k_rows_perm(RowJob j) {
 }
 
 // The same numeric pass from a recorded order without staging the products:
-// every run start reads its products straight from B (list index by a search
-// in the list ends, B position, column and value), four output positions
-// at a time so that their loads are in flight together.  Only the list
-// descriptors use shared memory, so many more warps fit an SM; used for the
-// rows of 32-key bins, whose staged form is limited by shared memory.
+// every run start reads its products straight from B (list index from a
+// per-row table of the positions' lists, B position, column and value), four
+// output positions at a time so that their loads are in flight together.
+// Only the list descriptors and that table use shared memory, so many more
+// warps fit an SM; used for the rows of 32-key bins, whose staged form is
+// limited by shared memory.
 template <class P>
 __device__ __noinline__ typename P::T perm_tree_reduce_direct(const uint16_t *pr, int P0, int N, const int32_t *d_off,
-                                                              const int32_t *d_q0, const typename P::In *d_a, int L,
-                                                              const typename P::In *bval) {
+                                                              const int32_t *d_q0, const typename P::In *d_a,
+                                                              const uint8_t *ltab, const typename P::In *bval) {
     using T = typename P::T;
     T V[kRegMaxDepth];
     int G[kRegMaxDepth];
@@ -759,7 +760,7 @@ __device__ __noinline__ typename P::T perm_tree_reduce_direct(const uint16_t *pr
         const uint32_t pe = pr[pos];
         if (pos > P0 && (pe & kPermStart)) break;
         const int p = (int)(pe & kPermPos);
-        const int l = find_last_le(d_off, L, p);
+        const int l = ltab[p];
         if (nv > 0) {
             const int d = 32 - __clz(prev_l ^ l);
             while (nv > 1 && G[nv - 1] < d) {
@@ -801,8 +802,11 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
     In *d_a = reinterpret_cast<In *>(desc);
     int32_t *d_q0 = reinterpret_cast<int32_t *>(desc + 8 * Cf::LCAP);
     int32_t *d_off = reinterpret_cast<int32_t *>(desc + 12 * Cf::LCAP);
+    // the list of every product position of the row (at most 256 lists)
+    uint8_t *ltab = smem + (size_t)nwarps * reg_stage_bytes(E) + (size_t)wid * 32 * E + (size_t)rho * Cf::CAP;
     const uint64_t keep = l2_keep_policy();
     const int stride = gridDim.x * nwarps * Cf::RPW;
+    static_assert(Cf::LCAP <= 256, "list indices must fit a byte");
 
     for (int r0 = (blockIdx.x * nwarps + wid) * Cf::RPW; r0 < j.count; r0 += stride) {
         const int slot = r0 + rho;
@@ -836,6 +840,18 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
         if (t == 0) d_off[0] = 0;
         const int N = carry;
         __syncwarp();
+        {
+            int l = 0;
+#pragma unroll 4
+            for (int i = 0; i < E; ++i) {
+                const int p = i * TPR + t;
+                if (p < N) {
+                    while (d_off[l + 1] <= p) ++l;
+                    ltab[p] = (uint8_t)l;
+                }
+            }
+        }
+        __syncwarp();
 
         const int64_t obase = has_row ? j.out_rp[row] : 0;
         const int cap = has_row ? (int)(j.out_rp[row + 1] - obase) : 0;
@@ -867,7 +883,7 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
                 q[b] = 0;
                 if (e[b] & kPermStart) {
                     const int p0 = (int)(e[b] & kPermPos);
-                    l[b] = find_last_le(d_off, L, p0);
+                    l[b] = ltab[p0];
                     q[b] = d_q0[l[b]] + (p0 - d_off[l[b]]);
                 }
             }
@@ -890,7 +906,7 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
                     const int w = count + __popc(msk & lt);
                     T val;
                     if (!(e[b] & kPermMulti)) val = P::mul(d_a[l[b]], v[b]);
-                    else val = perm_tree_reduce_direct<P>(pr, (j0 + b) * TPR + t, N, d_off, d_q0, d_a, L, ri.bval);
+                    else val = perm_tree_reduce_direct<P>(pr, (j0 + b) * TPR + t, N, d_off, d_q0, d_a, ltab, ri.bval);
                     if (w < cap) {
                         __stcs(ocol + w, c[b]);
                         __stcs(oval + w, P::fin(val));
@@ -909,7 +925,7 @@ __global__ void __launch_bounds__(256, 4) k_rows_perm_direct(RowJob j) {
 
 template <class P, int TPR, int E>
 cudaError_t launch_perm_direct_t(const RowJob &j, cudaStream_t st, int sms, int warps) {
-    const size_t sm = (size_t)warps * reg_stage_bytes(E);
+    const size_t sm = (size_t)warps * (reg_stage_bytes(E) + 32 * (size_t)E);
     auto kern = k_rows_perm_direct<P, TPR, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
