@@ -23,7 +23,10 @@
 // equal columns are added once, left list's value first.
 //
 // Buffers are plain pointers, so the same code runs on shared memory (warp and
-// block kernels) and on the device-memory arena (long rows).
+// block kernels) and on the device-memory arena (long rows).  In the arena a
+// round goes tile by tile through shared memory instead (merge_round_tiled):
+// the same merge, with the searches in device memory done once per tile end
+// rather than once per thread.
 #pragma once
 
 #include <cstdint>
@@ -498,13 +501,324 @@ __device__ __forceinline__ int merge_round(const G &g, int nl, const Buf<P> s, c
     return base;
 }
 
+// ---------------------------------------------------------------------------
+// One merging round in device memory, tile by tile through shared memory
+// (long rows).  The same merge as merge_round -- the same pairs, the same
+// merge-path cut into tiles of NT * K diagonals, left list first on ties --
+// but no thread searches device memory per tile: the block first finds the
+// pair and co-rank at the ends of NT tiles at once (one search per thread),
+// then every tile copies the elements its diagonals consume into shared
+// memory with independent coalesced loads, and each thread searches and
+// merges there.
+//
+// A tile [D0, D1) takes pairs m0 .. m1.  The diagonals of a tile consume
+// exactly D1 - D0 elements, laid out in shared memory as
+//   pair m0:        its left-list part, then its right-list part (both cut
+//                   at the tile's start co-rank, and at the end one when
+//                   m1 == m0);
+//   pairs m0+1 .. m1-1: whole, in buffer order;
+//   pair m1 > m0:   the left-list prefix, then the right-list prefix;
+// so that pair m > m0 starts at local position s.off[2m] - D0.  Three
+// elements outside the tile complete it: the left element before the tile
+// (a right element equal to it at the tile's start was already added), and
+// the next left and right elements after it (a left element at the tile's
+// end equal to the next right one adds that one's value).
+// ---------------------------------------------------------------------------
+template <class P, int NT, int K>
+struct TiledRoundSmem {
+    using T = typename P::T;
+    static constexpr int TS = NT * K;   // diagonals per tile
+    static constexpr int NB = NT + 1;   // tile ends per partition chunk (and the first start)
+    static constexpr int TAB = 2048;    // list offsets a tile stages (else read from device memory)
+    // per tile end: pair, co-rank, pair's left start / left end / right end,
+    // left element before, left element after, right element after (columns)
+    static constexpr int kFields = 8;
+    static constexpr size_t kVal = 0;
+    static constexpr size_t kCol = kVal + (P::kVal ? sizeof(T) * TS : 0);
+    static constexpr size_t kBV = align_up(kCol + sizeof(int32_t) * TS, 16);
+    static constexpr size_t kBI = align_up(kBV + (P::kVal ? sizeof(T) * NB : 0), 16);
+    static constexpr size_t kTab = align_up(kBI + sizeof(int32_t) * kFields * NB, 16);
+    static constexpr size_t kBytes = align_up(kTab + sizeof(int32_t) * TAB, 16);
+};
+
+// Pair and co-rank at diagonal D of a round (s, nl lists, np pairs), with the
+// pair's list bounds and the elements around the cut, into entry e.
+template <class P, int NB>
+__device__ __forceinline__ void tiled_cut(const Buf<P> s, int nl, int np, int D, int32_t *bi,
+                                          typename P::T *bv, int e) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s.off[2 * mid] <= D) lo = mid; else hi = mid - 1;
+    }
+    const int m = lo;
+    const int xs = s.off[2 * m], xl = s.off[2 * m + 1];
+    const int yl = (2 * m + 2 <= nl) ? s.off[2 * m + 2] : xl;
+    const int dd = D - xs;
+    int l = max(0, dd - (yl - xl)), h = min(dd, xl - xs);
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (s.col[xs + mid] <= s.col[xl + dd - 1 - mid]) l = mid + 1; else h = mid;
+    }
+    const int yp = xl + dd - l;
+    bi[0 * NB + e] = m;
+    bi[1 * NB + e] = l;
+    bi[2 * NB + e] = xs;
+    bi[3 * NB + e] = xl;
+    bi[4 * NB + e] = yl;
+    bi[5 * NB + e] = l > 0 ? s.col[xs + l - 1] : -1;
+    bi[6 * NB + e] = xs + l < xl ? s.col[xs + l] : kColEnd;
+    bi[7 * NB + e] = yp < yl ? s.col[yp] : kColEnd;
+    if constexpr (P::kVal) bv[e] = yp < yl ? s.val[yp] : typename P::T();
+}
+
+template <class P, int NT, int K, class Sink>
+__device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, const Sink &sink,
+                                 unsigned char *sm) {
+    using T = typename P::T;
+    using S = TiledRoundSmem<P, NT, K>;
+    constexpr int TS = S::TS, NB = S::NB;
+    T *tv = reinterpret_cast<T *>(sm + S::kVal);
+    int32_t *tc = reinterpret_cast<int32_t *>(sm + S::kCol);
+    T *bv = reinterpret_cast<T *>(sm + S::kBV);
+    int32_t *bi = reinterpret_cast<int32_t *>(sm + S::kBI);
+    int32_t *tab = reinterpret_cast<int32_t *>(sm + S::kTab);
+    const int tid = (int)threadIdx.x;
+    const int N = s.off[nl];
+    const int np = (nl + 1) >> 1;
+    const int ntiles = (int)(((int64_t)N + TS - 1) / TS);
+    int base = 0;
+    for (int c0 = 0; c0 < ntiles; c0 += NT) {
+        // cuts at the starts of tiles c0 .. c0 + NT (entry c - c0)
+        {
+            const int c = c0 + tid;
+            if (c <= ntiles) tiled_cut<P, NB>(s, nl, np, (int)min((int64_t)c * TS, (int64_t)N), bi, bv, tid);
+            if (tid == 0 && c0 + NT <= ntiles)
+                tiled_cut<P, NB>(s, nl, np, (int)min((int64_t)(c0 + NT) * TS, (int64_t)N), bi, bv, NT);
+        }
+        g.sync();
+        const int ce = min(ntiles, c0 + NT);
+        for (int c = c0; c < ce; ++c) {
+            const int ea = c - c0, eb = ea + 1;
+            const int D0 = c * TS, D1 = (int)min((int64_t)D0 + TS, (int64_t)N), TL = D1 - D0;
+            const int m0 = bi[0 * NB + ea], l0 = bi[1 * NB + ea], xs0 = bi[2 * NB + ea];
+            const int xl0 = bi[3 * NB + ea], yl0 = bi[4 * NB + ea];
+            const int m1 = bi[0 * NB + eb], l1 = bi[1 * NB + eb], xs1 = bi[2 * NB + eb], xl1 = bi[3 * NB + eb];
+            const int dd0 = D0 - xs0, dd1 = D1 - xs1;
+            const int nx0 = (m0 == m1 ? l1 : xl0 - xs0) - l0;
+            const int ny0 = (m0 == m1 ? dd1 - l1 : yl0 - xl0) - (dd0 - l0);
+            const int e0 = nx0 + ny0;
+            const int xb0 = xs0 + l0, yb0 = xl0 + dd0 - l0;
+            const int sl1 = xs1 - D0;
+            // stage the consumed elements
+            {
+                int src[K];
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    const int i = tid + u * NT;
+                    src[u] = -1;
+                    if (i < TL)
+                        src[u] = i < nx0 ? xb0 + i : i < e0 ? yb0 + (i - nx0) : i < sl1 + l1 ? D0 + i
+                                                                                              : xl1 + (i - sl1 - l1);
+                }
+                int32_t cc[K];
+                T vv[K];
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    if (src[u] >= 0) {
+                        cc[u] = s.col[src[u]];
+                        if constexpr (P::kVal) vv[u] = s.val[src[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    if (src[u] >= 0) {
+                        tc[tid + u * NT] = cc[u];
+                        if constexpr (P::kVal) tv[tid + u * NT] = vv[u];
+                    }
+                }
+            }
+            // stage the list offsets of pairs m0 .. m1
+            const int tlo = 2 * m0;
+            const int nent = min(2 * m1 + 2, nl) - tlo + 1;
+            const bool staged = nent <= S::TAB;
+            if (staged)
+                for (int i = tid; i < nent; i += NT) tab[i] = s.off[tlo + i];
+            g.sync();
+            auto off = [&](int idx) -> int {
+                return (staged && idx >= tlo && idx < tlo + nent) ? tab[idx - tlo] : s.off[idx];
+            };
+            const int px0 = bi[5 * NB + ea];
+            const int xe1 = bi[6 * NB + eb], ye1 = bi[7 * NB + eb];
+            T yev = T();
+            if constexpr (P::kVal) yev = bv[eb];
+
+            const int p0 = tid * K;
+            const int pend = min(p0 + K, TL);
+            int cnt = 0;
+            unsigned vmask = 0;
+            int32_t oc[K];
+            T ov[K];
+            int mfirst = 0, mlast = -1;
+            if (p0 < TL) {
+                // the pair holding local diagonal p0: the last one starting at or before it
+                int lo = m0, hi = m1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off(2 * mid) - D0 <= p0) lo = mid; else hi = mid - 1;
+                }
+                int m = lo;
+                // the pair's part of the tile: local start, left and right counts,
+                // the columns after both parts (and the value after the right one)
+                int sl, nx, ny, xe, ye;
+                T yv_e = T();
+                auto part = [&](int mm) {
+                    if (mm == m0) {
+                        sl = 0;
+                        nx = nx0;
+                        ny = ny0;
+                    } else {
+                        const int xsm = off(2 * mm), xlm = off(2 * mm + 1);
+                        sl = xsm - D0;
+                        if (mm == m1) {
+                            nx = l1;
+                            ny = dd1 - l1;
+                        } else {
+                            const int ylm = (2 * mm + 2 <= nl) ? off(2 * mm + 2) : xlm;
+                            nx = xlm - xsm;
+                            ny = ylm - xlm;
+                        }
+                    }
+                    if (mm == m1) {
+                        xe = xe1;
+                        ye = ye1;
+                        yv_e = yev;
+                    } else {
+                        xe = kColEnd;
+                        ye = kColEnd;
+                    }
+                };
+                part(m);
+                const int dd = p0 - sl;
+                int l = max(0, dd - ny), h = min(dd, nx);
+                while (l < h) {
+                    const int mid = (l + h) >> 1;
+                    if (tc[sl + mid] <= tc[sl + nx + dd - 1 - mid]) l = mid + 1; else h = mid;
+                }
+                int xi = l, yj = dd - l;
+                if constexpr (Sink::kOffsets) {
+                    if (dd == 0 && (m != m0 || dd0 == 0)) {
+                        // pair m -- and any empty pairs right before it -- start here
+                        const int st = off(2 * m);
+                        mfirst = m;
+                        while (mfirst > 0 && off(2 * (mfirst - 1)) == st) --mfirst;
+                        for (int mm = mfirst; mm <= m; ++mm) sink.d.off[mm] = 0;
+                        mlast = m;
+                    }
+                }
+                int32_t xc = xi < nx ? tc[sl + xi] : xe;
+                int32_t yc = yj < ny ? tc[sl + nx + yj] : ye;
+                T xv = T(), yv = T();
+                if constexpr (P::kVal) {
+                    if (xi < nx) xv = tv[sl + xi];
+                    yv = yj < ny ? tv[sl + nx + yj] : yv_e;
+                }
+                // a right element equal to the left one before it was added by
+                // that one's diagonal
+                const int32_t xprev = xi > 0 ? tc[sl + xi - 1] : (m == m0 && l0 > 0 ? px0 : -1);
+                bool skip = yj < ny && xprev == yc;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (p0 + k < pend) {
+                        if (skip) {
+                            skip = false;
+                            ++yj;
+                            yc = yj < ny ? tc[sl + nx + yj] : ye;
+                            if constexpr (P::kVal) yv = yj < ny ? tv[sl + nx + yj] : yv_e;
+                        } else {
+                            while (xi >= nx && yj >= ny && m < m1) {
+                                // this pair's part is done; the next pair starts here
+                                ++m;
+                                part(m);
+                                xi = 0;
+                                yj = 0;
+                                if constexpr (Sink::kOffsets) {
+                                    sink.d.off[m] = cnt;
+                                    if (mlast < 0) mfirst = m;
+                                    mlast = m;
+                                }
+                                xc = nx > 0 ? tc[sl] : xe;
+                                yc = ny > 0 ? tc[sl + nx] : ye;
+                                if constexpr (P::kVal) {
+                                    if (nx > 0) xv = tv[sl];
+                                    yv = ny > 0 ? tv[sl + nx] : yv_e;
+                                }
+                            }
+                            int32_t c;
+                            T v;
+                            if (xc <= yc) {
+                                c = xc;
+                                v = xv;
+                                if (xc == yc) { v = P::add(xv, yv); skip = true; }
+                                ++xi;
+                                xc = xi < nx ? tc[sl + xi] : xe;
+                                if constexpr (P::kVal) { if (xi < nx) xv = tv[sl + xi]; }
+                            } else {
+                                c = yc;
+                                v = yv;
+                                ++yj;
+                                yc = yj < ny ? tc[sl + nx + yj] : ye;
+                                if constexpr (P::kVal) yv = yj < ny ? tv[sl + nx + yj] : yv_e;
+                            }
+                            oc[k] = c;
+                            ov[k] = v;
+                            vmask |= 1u << k;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+            int tot;
+            const int ex = g.scan_excl(cnt, tot);   // also: every thread is done with the tile
+            int w = base + ex;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if ((vmask >> k) & 1u) {
+                    sink.put(w, oc[k], ov[k]);
+                    ++w;
+                }
+            }
+            if constexpr (Sink::kOffsets) {
+                for (int mm = mfirst; mm <= mlast; ++mm) sink.d.off[mm] += base + ex;
+            }
+            base += tot;
+        }
+        g.sync();   // the cuts are replaced by the next chunk's
+    }
+    if constexpr (Sink::kOffsets) {
+        // pairs that start after the last element (trailing empty lists) and the end
+        for (int m = tid; m < np; m += NT)
+            if (s.off[2 * m] == N) sink.d.off[m] = base;
+        if (tid == 0) sink.d.off[np] = base;
+    }
+    g.sync();
+    return base;
+}
+
+template <bool kTiled, class P, class G, int K, class Sink>
+__device__ __forceinline__ int round_of(const G &g, int nl, const Buf<P> s, const Sink &sink, unsigned char *tsm) {
+    if constexpr (kTiled) return merge_round_tiled<P, G::N, K>(g, nl, s, sink, tsm);
+    else return merge_round<P, G, K>(g, nl, s, sink);
+}
+
 // Whole row (Algorithm 1 for one i): the multiplying phase into b0, merging
 // rounds between b0 and b1 while more than two lists are left, then the last
 // round -- or, for a row of one list, a copy -- into the row's output slot
 // (the last line of Algorithm 1).  Numeric passes write C (or C_bar) at
 // out_rp[row]; every pass may record the row length in out_cnt[row].
-template <class P, class G, int K, int UNR>
-__device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1) {
+template <class P, class G, int K, int UNR, bool kTiled = false>
+__device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1,
+                                        unsigned char *tsm = nullptr) {
     using In = typename P::In;
     const RowIn<In> ri = row_in<In>(j, row);
     const int L = ri.L;
@@ -512,7 +826,7 @@ __device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, co
     Buf<P> s = b0, d = b1;
     int nl = L;
     while (nl > 2) {
-        merge_round<P, G, K>(g, nl, s, BufSink<P>{d});
+        round_of<kTiled, P, G, K>(g, nl, s, BufSink<P>{d}, tsm);
         const Buf<P> t = s; s = d; d = t;
         nl = (nl + 1) >> 1;
     }
@@ -523,7 +837,7 @@ __device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, co
         const int cap = (int)(j.out_rp[row + 1] - base);
         const OutSink<P> out{j.out_col + base, static_cast<typename P::Out *>(j.out_val) + base, cap};
         if (nl == 2) {
-            len = merge_round<P, G, K>(g, nl, s, out);
+            len = round_of<kTiled, P, G, K>(g, nl, s, out, tsm);
         } else {
             len = s.off[nl];
             for (int p = g.rank(); p < len; p += G::N) out.put(p, s.col[p], s.val[p]);
@@ -532,7 +846,7 @@ __device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, co
             if (g.rank() == 0) atomicOr(j.err, 1u);
         }
     } else {
-        if (nl == 2) len = merge_round<P, G, K>(g, nl, s, CountSink<P>{});
+        if (nl == 2) len = round_of<kTiled, P, G, K>(g, nl, s, CountSink<P>{}, tsm);
         else len = s.off[nl];
     }
     if (j.out_cnt != nullptr && g.rank() == 0) j.out_cnt[row] = len;

@@ -7,7 +7,8 @@
 //              buffers in shared memory.
 //   long bin   everything else: one thread block per row; by column buckets
 //              (brm_long_rows.cuh) or by merge rounds in a device-memory
-//              arena slice given per row by the host (this file).
+//              arena slice given per row by the host (this file), each round
+//              tile by tile through shared memory (merge_round_tiled).
 // Rows are taken from the bin's row list in a grid-stride loop.
 #pragma once
 
@@ -104,6 +105,7 @@ __host__ __device__ constexpr size_t long_row_bytes(int64_t n, int64_t L) { retu
 
 template <class P>
 __global__ void __launch_bounds__(kLongThreads, 2) k_rows_long(RowJob j) {
+    extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ int ws[kLongThreads / 32 + 1];
     BlockGrp<kLongThreads> g;
     g.ws = ws;
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_rows_long(RowJob j) {
         b1.col = reinterpret_cast<int32_t *>(p + lay.col1);
         b0.off = reinterpret_cast<int32_t *>(p + lay.off0);
         b1.off = reinterpret_cast<int32_t *>(p + lay.off1);
-        brm_row<P, BlockGrp<kLongThreads>, long_k<P>(), 4>(g, row, j, b0, b1);
+        brm_row<P, BlockGrp<kLongThreads>, long_k<P>(), 4, true>(g, row, j, b0, b1, tsm);
     }
 }
 
@@ -172,7 +174,12 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
     }
     // long rows: one block per row of the batch
     if (j.long_bucket) return launch_long_bucket<P>(j, st);
-    k_rows_long<P><<<j.count, kLongThreads, 0, st>>>(j);
+    {
+        const size_t sm = TiledRoundSmem<P, kLongThreads, long_k<P>()>::kBytes;
+        cudaError_t e = cudaFuncSetAttribute(k_rows_long<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_rows_long<P><<<j.count, kLongThreads, sm, st>>>(j);
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -172,3 +172,21 @@ def test_batched_long_rows():
     torch.cuda.synchronize()
     for Cp, (A, B) in zip(brm.split(C, off, [B1.cols, B2.cols]), [(A1, B1), (A2, B2)]):
         assert_rows_exact(Cp, oracle.alg1(A, B))
+
+
+@pytest.mark.parametrize("mode,dtype,comp", MODES)
+def test_arena_rounds_many_tiles_and_empty_pairs(mode, dtype, comp):
+    """The merge rounds in the arena, tile by tile: a row of 1.2 M products
+    (more than 512 tiles in its first rounds, so the tile cuts are found in
+    two chunks) and a row of 57000 lists, nearly all empty (a tile spans more
+    pairs than it stages list offsets for)."""
+    k, ncols = 60000, 50000
+    rnd = (I.rand_u64(103, 1, np.arange(3000 * 400)) % np.uint64(ncols)).astype(np.int64).reshape(3000, 400)
+    rows = [np.unique(r) for r in rnd]
+    rows += [np.arange(t % 97, ncols, 1000) if t % 1000 == 0 else np.zeros(0, np.int64) for t in range(3000, k)]
+    B = csr_from_rows(rows, ncols, 104, 1)
+    A = csr_from_rows([np.arange(3000), np.arange(3000, k), np.array([5, 3000, 4000, 59000])], k, 105, 2)
+    ref = oracle.alg1(A, B, prec=mode)
+    C = run(A, B, "precise", dtype, comp, long_bucket=False)
+    assert_rows_exact(C, ref)
+    same(C, run(A, B, "upper", dtype, comp, long_bucket=False))
