@@ -528,17 +528,22 @@ template <class P, int NT, int K>
 struct TiledRoundSmem {
     using T = typename P::T;
     static constexpr int TS = NT * K;   // diagonals per tile
-    static constexpr int NB = NT + 1;   // tile ends per partition chunk (and the first start)
-    static constexpr int TAB = 2048;    // list offsets a tile stages (else read from device memory)
+    static constexpr int CH = NT / 4;   // tiles per partition chunk
+    static constexpr int NB = CH + 1;   // cuts per chunk: the chunk's tile starts and its end
+    static constexpr int TAB = 1024;    // list offsets a tile stages (else read from device memory)
     // per tile end: pair, co-rank, pair's left start / left end / right end,
     // left element before, left element after, right element after (columns)
     static constexpr int kFields = 8;
+    // two tiles (the next one is loaded while the current one is merged)
     static constexpr size_t kVal = 0;
-    static constexpr size_t kCol = kVal + (P::kVal ? sizeof(T) * TS : 0);
-    static constexpr size_t kBV = align_up(kCol + sizeof(int32_t) * TS, 16);
+    static constexpr size_t kCol = kVal + (P::kVal ? 2 * sizeof(T) * TS : 0);
+    static constexpr size_t kBV = align_up(kCol + 2 * sizeof(int32_t) * TS, 16);
     static constexpr size_t kBI = align_up(kBV + (P::kVal ? sizeof(T) * NB : 0), 16);
     static constexpr size_t kTab = align_up(kBI + sizeof(int32_t) * kFields * NB, 16);
-    static constexpr size_t kBytes = align_up(kTab + sizeof(int32_t) * TAB, 16);
+    // each thread's merged elements, diagonal k of thread t at k * NT + t
+    static constexpr size_t kOV = align_up(kTab + 2 * sizeof(int32_t) * TAB, 16);
+    static constexpr size_t kOC = kOV + (P::kVal ? sizeof(T) * TS : 0);
+    static constexpr size_t kBytes = align_up(kOC + sizeof(int32_t) * TS, 16);
 };
 
 // Pair and co-rank at diagonal D of a round (s, nl lists, np pairs), with the
@@ -572,79 +577,108 @@ __device__ __forceinline__ void tiled_cut(const Buf<P> s, int nl, int np, int D,
     if constexpr (P::kVal) bv[e] = yp < yl ? s.val[yp] : typename P::T();
 }
 
+// Asynchronous 4- and 8-byte copies device memory -> shared memory.
+__device__ __forceinline__ void tiled_cp4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+template <class T>
+__device__ __forceinline__ void tiled_cpv(T *dst, const T *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tiled_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tiled_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Issues the copies of tile c (cut entries ea = c - c0 and ea + 1) into one
+// of the two tile buffers: the elements its diagonals consume, in the order
+// described above, and the list offsets of its pairs when they fit.
+template <class P, int NT, int K>
+__device__ __forceinline__ void tiled_stage(const Buf<P> s, int nl, int N, int c, int ea, const int32_t *bi,
+                                            int32_t *tc, typename P::T *tv, int32_t *tab) {
+    using S = TiledRoundSmem<P, NT, K>;
+    constexpr int TS = S::TS, NB = S::NB;
+    const int tid = (int)threadIdx.x;
+    const int eb = ea + 1;
+    const int D0 = c * TS, TL = (int)min((int64_t)TS, (int64_t)N - D0);
+    const int m0 = bi[0 * NB + ea], l0 = bi[1 * NB + ea], xs0 = bi[2 * NB + ea];
+    const int xl0 = bi[3 * NB + ea], yl0 = bi[4 * NB + ea];
+    const int m1 = bi[0 * NB + eb], l1 = bi[1 * NB + eb], xs1 = bi[2 * NB + eb], xl1 = bi[3 * NB + eb];
+    const int dd0 = D0 - xs0, dd1 = D0 + TL - xs1;
+    const int nx0 = (m0 == m1 ? l1 : xl0 - xs0) - l0;
+    const int ny0 = (m0 == m1 ? dd1 - l1 : yl0 - xl0) - (dd0 - l0);
+    const int e0 = nx0 + ny0;
+    const int xb0 = xs0 + l0, yb0 = xl0 + dd0 - l0;
+    const int sl1 = xs1 - D0;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const int i = tid + u * NT;
+        if (i < TL) {
+            const int src = i < nx0 ? xb0 + i : i < e0 ? yb0 + (i - nx0) : i < sl1 + l1 ? D0 + i : xl1 + (i - sl1 - l1);
+            tiled_cp4(tc + i, s.col + src);
+            if constexpr (P::kVal) tiled_cpv(tv + i, s.val + src);
+        }
+    }
+    const int tlo = 2 * m0;
+    const int nent = min(2 * m1 + 2, nl) - tlo + 1;
+    if (nent <= S::TAB)
+        for (int i = tid; i < nent; i += NT) tiled_cp4(tab + i, s.off + tlo + i);
+    tiled_cp_commit();
+}
+
 template <class P, int NT, int K, class Sink>
 __device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, const Sink &sink,
                                  unsigned char *sm) {
     using T = typename P::T;
     using S = TiledRoundSmem<P, NT, K>;
     constexpr int TS = S::TS, NB = S::NB;
-    T *tv = reinterpret_cast<T *>(sm + S::kVal);
-    int32_t *tc = reinterpret_cast<int32_t *>(sm + S::kCol);
+    T *tv0 = reinterpret_cast<T *>(sm + S::kVal);
+    int32_t *tc0 = reinterpret_cast<int32_t *>(sm + S::kCol);
     T *bv = reinterpret_cast<T *>(sm + S::kBV);
     int32_t *bi = reinterpret_cast<int32_t *>(sm + S::kBI);
-    int32_t *tab = reinterpret_cast<int32_t *>(sm + S::kTab);
+    int32_t *tab0 = reinterpret_cast<int32_t *>(sm + S::kTab);
+    T *ovs = reinterpret_cast<T *>(sm + S::kOV);
+    int32_t *ocs = reinterpret_cast<int32_t *>(sm + S::kOC);
     const int tid = (int)threadIdx.x;
     const int N = s.off[nl];
     const int np = (nl + 1) >> 1;
     const int ntiles = (int)(((int64_t)N + TS - 1) / TS);
     int base = 0;
-    for (int c0 = 0; c0 < ntiles; c0 += NT) {
-        // cuts at the starts of tiles c0 .. c0 + NT (entry c - c0)
+    for (int c0 = 0; c0 < ntiles; c0 += S::CH) {
+        // cuts at the starts of tiles c0 .. c0 + CH (entry c - c0)
         {
             const int c = c0 + tid;
-            if (c <= ntiles) tiled_cut<P, NB>(s, nl, np, (int)min((int64_t)c * TS, (int64_t)N), bi, bv, tid);
-            if (tid == 0 && c0 + NT <= ntiles)
-                tiled_cut<P, NB>(s, nl, np, (int)min((int64_t)(c0 + NT) * TS, (int64_t)N), bi, bv, NT);
+            if (tid <= S::CH && c <= ntiles)
+                tiled_cut<P, NB>(s, nl, np, (int)min((int64_t)c * TS, (int64_t)N), bi, bv, tid);
         }
         g.sync();
-        const int ce = min(ntiles, c0 + NT);
+        const int ce = min(ntiles, c0 + S::CH);
+        tiled_stage<P, NT, K>(s, nl, N, c0, 0, bi, tc0 + (c0 & 1) * TS, tv0 + (c0 & 1) * TS, tab0 + (c0 & 1) * S::TAB);
         for (int c = c0; c < ce; ++c) {
+            // tile c is in buffer c & 1; every thread is done with tile c - 1,
+            // whose buffer takes tile c + 1
+            tiled_cp_wait();
+            g.sync();
+            if (c + 1 < ce)
+                tiled_stage<P, NT, K>(s, nl, N, c + 1, c + 1 - c0, bi, tc0 + ((c + 1) & 1) * TS,
+                                      tv0 + ((c + 1) & 1) * TS, tab0 + ((c + 1) & 1) * S::TAB);
+            const int32_t *tc = tc0 + (c & 1) * TS;
+            const T *tv = tv0 + (c & 1) * TS;
+            const int32_t *tab = tab0 + (c & 1) * S::TAB;
             const int ea = c - c0, eb = ea + 1;
             const int D0 = c * TS, D1 = (int)min((int64_t)D0 + TS, (int64_t)N), TL = D1 - D0;
             const int m0 = bi[0 * NB + ea], l0 = bi[1 * NB + ea], xs0 = bi[2 * NB + ea];
             const int xl0 = bi[3 * NB + ea], yl0 = bi[4 * NB + ea];
-            const int m1 = bi[0 * NB + eb], l1 = bi[1 * NB + eb], xs1 = bi[2 * NB + eb], xl1 = bi[3 * NB + eb];
+            const int m1 = bi[0 * NB + eb], l1 = bi[1 * NB + eb], xs1 = bi[2 * NB + eb];
             const int dd0 = D0 - xs0, dd1 = D1 - xs1;
             const int nx0 = (m0 == m1 ? l1 : xl0 - xs0) - l0;
             const int ny0 = (m0 == m1 ? dd1 - l1 : yl0 - xl0) - (dd0 - l0);
-            const int e0 = nx0 + ny0;
-            const int xb0 = xs0 + l0, yb0 = xl0 + dd0 - l0;
-            const int sl1 = xs1 - D0;
-            // stage the consumed elements
-            {
-                int src[K];
-#pragma unroll
-                for (int u = 0; u < K; ++u) {
-                    const int i = tid + u * NT;
-                    src[u] = -1;
-                    if (i < TL)
-                        src[u] = i < nx0 ? xb0 + i : i < e0 ? yb0 + (i - nx0) : i < sl1 + l1 ? D0 + i
-                                                                                              : xl1 + (i - sl1 - l1);
-                }
-                int32_t cc[K];
-                T vv[K];
-#pragma unroll
-                for (int u = 0; u < K; ++u) {
-                    if (src[u] >= 0) {
-                        cc[u] = s.col[src[u]];
-                        if constexpr (P::kVal) vv[u] = s.val[src[u]];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < K; ++u) {
-                    if (src[u] >= 0) {
-                        tc[tid + u * NT] = cc[u];
-                        if constexpr (P::kVal) tv[tid + u * NT] = vv[u];
-                    }
-                }
-            }
-            // stage the list offsets of pairs m0 .. m1
             const int tlo = 2 * m0;
             const int nent = min(2 * m1 + 2, nl) - tlo + 1;
             const bool staged = nent <= S::TAB;
-            if (staged)
-                for (int i = tid; i < nent; i += NT) tab[i] = s.off[tlo + i];
-            g.sync();
             auto off = [&](int idx) -> int {
                 return (staged && idx >= tlo && idx < tlo + nent) ? tab[idx - tlo] : s.off[idx];
             };
@@ -657,8 +691,6 @@ __device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, 
             const int pend = min(p0 + K, TL);
             int cnt = 0;
             unsigned vmask = 0;
-            int32_t oc[K];
-            T ov[K];
             int mfirst = 0, mlast = -1;
             if (p0 < TL) {
                 // the pair holding local diagonal p0: the last one starting at or before it
@@ -716,65 +748,61 @@ __device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, 
                         mlast = m;
                     }
                 }
-                int32_t xc = xi < nx ? tc[sl + xi] : xe;
-                int32_t yc = yj < ny ? tc[sl + nx + yj] : ye;
+                // current left and right elements (the columns after a part
+                // when it is used up); loads are clamped into the tile and the
+                // result selected, so that the lanes of a warp do not diverge
+                int32_t xc, yc;
                 T xv = T(), yv = T();
-                if constexpr (P::kVal) {
-                    if (xi < nx) xv = tv[sl + xi];
-                    yv = yj < ny ? tv[sl + nx + yj] : yv_e;
-                }
-                // a right element equal to the left one before it was added by
-                // that one's diagonal
-                const int32_t xprev = xi > 0 ? tc[sl + xi - 1] : (m == m0 && l0 > 0 ? px0 : -1);
-                bool skip = yj < ny && xprev == yc;
+                auto load_x = [&]() {
+                    const int i = min(sl + xi, TS - 1);
+                    const bool in = xi < nx;
+                    xc = in ? tc[i] : xe;
+                    if constexpr (P::kVal) xv = tv[i];
+                };
+                auto load_y = [&]() {
+                    const int i = min(sl + nx + yj, TS - 1);
+                    const bool in = yj < ny;
+                    yc = in ? tc[i] : ye;
+                    if constexpr (P::kVal) { const T t = tv[i]; yv = in ? t : yv_e; }
+                };
+                load_x();
+                load_y();
+                // column of the last left element taken: a right element equal
+                // to it was added by that element's diagonal and is skipped
+                int32_t lastx = xi > 0 ? tc[sl + xi - 1] : (m == m0 && l0 > 0 ? px0 : -1);
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     if (p0 + k < pend) {
-                        if (skip) {
-                            skip = false;
-                            ++yj;
-                            yc = yj < ny ? tc[sl + nx + yj] : ye;
-                            if constexpr (P::kVal) yv = yj < ny ? tv[sl + nx + yj] : yv_e;
-                        } else {
-                            while (xi >= nx && yj >= ny && m < m1) {
-                                // this pair's part is done; the next pair starts here
-                                ++m;
-                                part(m);
-                                xi = 0;
-                                yj = 0;
-                                if constexpr (Sink::kOffsets) {
-                                    sink.d.off[m] = cnt;
-                                    if (mlast < 0) mfirst = m;
-                                    mlast = m;
-                                }
-                                xc = nx > 0 ? tc[sl] : xe;
-                                yc = ny > 0 ? tc[sl + nx] : ye;
-                                if constexpr (P::kVal) {
-                                    if (nx > 0) xv = tv[sl];
-                                    yv = ny > 0 ? tv[sl + nx] : yv_e;
-                                }
+                        while (xi >= nx && yj >= ny && m < m1) {
+                            // this pair's part is done; the next pair starts here
+                            ++m;
+                            part(m);
+                            xi = 0;
+                            yj = 0;
+                            if constexpr (Sink::kOffsets) {
+                                sink.d.off[m] = cnt;
+                                if (mlast < 0) mfirst = m;
+                                mlast = m;
                             }
-                            int32_t c;
-                            T v;
-                            if (xc <= yc) {
-                                c = xc;
-                                v = xv;
-                                if (xc == yc) { v = P::add(xv, yv); skip = true; }
-                                ++xi;
-                                xc = xi < nx ? tc[sl + xi] : xe;
-                                if constexpr (P::kVal) { if (xi < nx) xv = tv[sl + xi]; }
-                            } else {
-                                c = yc;
-                                v = yv;
-                                ++yj;
-                                yc = yj < ny ? tc[sl + nx + yj] : ye;
-                                if constexpr (P::kVal) yv = yj < ny ? tv[sl + nx + yj] : yv_e;
-                            }
-                            oc[k] = c;
-                            ov[k] = v;
-                            vmask |= 1u << k;
-                            ++cnt;
+                            lastx = -1;
+                            load_x();
+                            load_y();
                         }
+                        const bool takex = xc <= yc;
+                        const bool skip = !takex && yc == lastx;
+                        T v = yv;
+                        if constexpr (P::kVal) {
+                            const T sum = P::add(xv, yv);
+                            v = takex ? (xc == yc ? sum : xv) : yv;
+                        }
+                        ocs[k * NT + tid] = takex ? xc : yc;
+                        if constexpr (P::kVal) ovs[k * NT + tid] = v;
+                        vmask |= (skip ? 0u : 1u) << k;
+                        cnt += skip ? 0 : 1;
+                        lastx = takex ? xc : lastx;
+                        xi += takex ? 1 : 0;
+                        yj += takex ? 0 : 1;
+                        if (takex) load_x(); else load_y();
                     }
                 }
             }
@@ -784,7 +812,7 @@ __device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, 
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if ((vmask >> k) & 1u) {
-                    sink.put(w, oc[k], ov[k]);
+                    sink.put(w, ocs[k * NT + tid], P::kVal ? ovs[k * NT + tid] : T());
                     ++w;
                 }
             }
