@@ -806,8 +806,29 @@ __device__ int merge_round_tiled(const BlockGrp<NT> &g, int nl, const Buf<P> s, 
                     }
                 }
             }
-            int tot;
-            const int ex = g.scan_excl(cnt, tot);   // also: every thread is done with the tile
+            // exclusive prefix of the counts over the block with one barrier:
+            // the warp sums are read again only after the next tile's barrier
+            int tot, ex;
+            {
+                const int lane = tid & 31, wid = tid >> 5;
+                int v = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, v, d);
+                    if (lane >= d) v += u;
+                }
+                if (lane == 31) g.ws[wid] = v;
+                g.sync();
+                const int ws_l = lane < BlockGrp<NT>::NW ? g.ws[lane] : 0;
+                int w = ws_l;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, w, d);
+                    if (lane >= d) w += u;
+                }
+                tot = __shfl_sync(0xffffffffu, w, BlockGrp<NT>::NW - 1);
+                ex = __shfl_sync(0xffffffffu, w - ws_l, wid) + v - cnt;
+            }
             int w = base + ex;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
