@@ -506,10 +506,12 @@ __device__ __forceinline__ int merge_round(const G &g, int nl, const Buf<P> s, c
 // (long rows).  The same merge as merge_round -- the same pairs, the same
 // merge-path cut into tiles of NT * K diagonals, left list first on ties --
 // but no thread searches device memory per tile: the block first finds the
-// pair and co-rank at the ends of NT tiles at once (one search per thread),
-// then every tile copies the elements its diagonals consume into shared
-// memory with independent coalesced loads, and each thread searches and
-// merges there.
+// pair and co-rank at the ends of NT / 4 tiles at once (one search per
+// thread), then every tile's consumed elements are copied into shared memory
+// with cp.async (the next tile's while the current one merges), and each
+// thread searches and merges there, K steps without divergent branches
+// (left or right, tie and skip are selects), into a shared-memory buffer
+// that it copies out after the block's prefix sum of the counts.
 //
 // A tile [D0, D1) takes pairs m0 .. m1.  The diagonals of a tile consume
 // exactly D1 - D0 elements, laid out in shared memory as
