@@ -150,8 +150,12 @@ typedef struct {
  *                  counts those rows' columns in a shared-memory bitmap when B
  *                  has at most 2^24 columns.)
  *   arena_bytes    budget of the device-memory arena for long rows (0 = the
- *                  library picks 1/8 of free memory, at least enough for the
- *                  longest row).
+ *                  library picks 1/4 of free memory, at most 64 GiB, for the
+ *                  merge rounds -- persistent blocks, each holding one row's
+ *                  buffers at a time -- or 1/8, at most 32 GiB, for the
+ *                  column-bucket batches; always at least enough for the
+ *                  longest row).  A smaller budget runs fewer persistent
+ *                  blocks (merge rounds) or more batches (column buckets).
  *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
  *                  sizeof value) bytes) processed at once; a larger product
  *                  is processed in row chunks of at most this size, each

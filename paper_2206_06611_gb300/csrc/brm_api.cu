@@ -406,8 +406,13 @@ struct LongPlan {
     // arena (after its rows), and its capacity in records
     std::vector<int64_t> work_off, work_cap;
     int64_t slots_bytes = 0, work_bytes_max = 0;
-    int64_t *off_d = nullptr;       // device: arena offset of every long slot
+    int64_t *off_d = nullptr;       // device: arena offset of every long slot (merge rounds: of every block)
     char *arena = nullptr;
+    // merge rounds: one launch of `grid` persistent blocks; block b takes
+    // slot b, then the next slot from the counter; its arena holds the
+    // largest of the slots it can get
+    int32_t grid = 0;
+    int32_t *ctr = nullptr;
 };
 
 int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp) {
@@ -431,19 +436,47 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = (size_t)8 << 30; }
-        budget = std::min<size_t>(fr / 8, (size_t)32 << 30);
+        budget = lp.bucket ? std::min<size_t>(fr / 8, (size_t)32 << 30) : std::min<size_t>(fr / 4, (size_t)64 << 30);
     }
     budget = std::max(budget, biggest);
     std::vector<int64_t> off(nl);
-    size_t cur = 0, maxbatch = 0;
-    for (int64_t s = 0; s < nl; ++s) {
-        if (s == 0 || cur + (size_t)need[s] > budget) {
-            lp.starts.push_back(s);
-            cur = 0;
+    size_t maxbatch = 0;
+    lp.grid = 0;
+    if (!lp.bucket) {
+        // merge rounds: the slots are sorted by product count, largest first.
+        // Block b < R merges slot b and then slots R, R + 1, ... from a
+        // counter; its arena holds max(need[b], the largest need after R).
+        // R is the resident block count, lowered until the arena fits.
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<int64_t> tailmax(nl + 1, 0);
+        for (int64_t s = nl - 1; s >= 0; --s) tailmax[s] = std::max(tailmax[s + 1], need[s]);
+        int64_t R = std::min<int64_t>(nl, 2 * (int64_t)std::max(sms, 1));
+        for (;; --R) {
+            size_t sum = 0;
+            for (int64_t b = 0; b < R; ++b) sum += (size_t)std::max(need[b], tailmax[R]);
+            if (sum <= budget || R == 1) break;
         }
-        off[s] = (int64_t)cur;
-        cur += (size_t)need[s];
-        maxbatch = std::max(maxbatch, cur);
+        size_t cur = 0;
+        for (int64_t b = 0; b < R; ++b) {
+            off[b] = (int64_t)cur;
+            cur += (size_t)std::max(need[b], tailmax[R]);
+        }
+        maxbatch = cur;
+        lp.grid = (int32_t)R;
+        lp.starts.push_back(0);
+    } else {
+        size_t cur = 0;
+        for (int64_t s = 0; s < nl; ++s) {
+            if (s == 0 || cur + (size_t)need[s] > budget) {
+                lp.starts.push_back(s);
+                cur = 0;
+            }
+            off[s] = (int64_t)cur;
+            cur += (size_t)need[s];
+            maxbatch = std::max(maxbatch, cur);
+        }
     }
     lp.starts.push_back(nl);
     lp.work_off.clear();
@@ -473,6 +506,7 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
     int rc = get(mem, lp.off_d, nl, "arena offsets");
     if (rc) return rc;
     if ((rc = get(mem, lp.arena, maxbatch, "long-row arena"))) return rc;
+    if (!lp.bucket && (rc = get(mem, lp.ctr, 1, "long-row counter"))) return rc;
     BRM_CUDA(cudaMemcpyAsync(lp.off_d, off.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
     return BRM_OK;
@@ -508,6 +542,11 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
             jb.lb_cap = lp.work_cap[bi];
         }
         jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
+        if (lp.grid > 0) {
+            jb.long_grid = lp.grid;
+            jb.long_ctr = lp.ctr;
+            BRM_CUDA(cudaMemsetAsync(lp.ctr, 0, sizeof(int32_t), st));
+        }
         BRM_CUDA(launch_rows(v, kBinLong, jb, st));
     }
     return BRM_OK;

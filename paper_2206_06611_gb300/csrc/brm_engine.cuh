@@ -213,6 +213,11 @@ struct RowJob {
     char *arena;
     const int64_t *arena_off;
     const int64_t *slot_nprod;
+    // merge rounds in the arena: long_grid > 0 launches that many persistent
+    // blocks; block b takes slot b, then slots long_grid, long_grid + 1, ...
+    // from the counter (zero at launch), in the arena at arena_off[b]
+    int32_t *long_ctr;
+    int32_t long_grid;
 };
 
 // The inputs one output row needs: its row of A (columns and values from the

@@ -107,14 +107,18 @@ template <class P>
 __global__ void __launch_bounds__(kLongThreads, 2) k_rows_long(RowJob j) {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ int ws[kLongThreads / 32 + 1];
+    __shared__ int s_next;
     BlockGrp<kLongThreads> g;
     g.ws = ws;
     using T = typename P::T;
-    for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
+    // persistent blocks (long_grid > 0): slot blockIdx.x first, then slots
+    // from the counter, all in this block's arena; else one slot per block
+    const bool pers = j.long_grid > 0;
+    unsigned char *p = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[blockIdx.x];
+    for (int r = blockIdx.x; r < j.count;) {
         const int row = j.rows[r];
         const int64_t n = j.slot_nprod[r];
         const int L = row_in<typename P::In>(j, row).L;
-        unsigned char *p = reinterpret_cast<unsigned char *>(j.arena) + j.arena_off[r];
         const LongLayout lay = long_layout<P>(n, L);
         Buf<P> b0, b1;
         if constexpr (P::kVal) {
@@ -129,6 +133,11 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_rows_long(RowJob j) {
         b0.off = reinterpret_cast<int32_t *>(p + lay.off0);
         b1.off = reinterpret_cast<int32_t *>(p + lay.off1);
         brm_row<P, BlockGrp<kLongThreads>, long_k<P>(), 4, true>(g, row, j, b0, b1, tsm);
+        if (!pers) break;
+        if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(j.long_ctr, 1);
+        __syncthreads();
+        r = s_next;
+        __syncthreads();   // s_next is rewritten only after every thread has read it
     }
 }
 
@@ -178,7 +187,8 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
         const size_t sm = TiledRoundSmem<P, kLongThreads, long_k<P>()>::kBytes;
         cudaError_t e = cudaFuncSetAttribute(k_rows_long<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_rows_long<P><<<j.count, kLongThreads, sm, st>>>(j);
+        const int grid = j.long_grid > 0 ? min(j.long_grid, j.count) : j.count;
+        k_rows_long<P><<<grid, kLongThreads, sm, st>>>(j);
     }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

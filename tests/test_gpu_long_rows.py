@@ -190,3 +190,18 @@ def test_arena_rounds_many_tiles_and_empty_pairs(mode, dtype, comp):
     C = run(A, B, "precise", dtype, comp, long_bucket=False)
     assert_rows_exact(C, ref)
     same(C, run(A, B, "upper", dtype, comp, long_bucket=False))
+
+
+@pytest.mark.parametrize("mode,dtype,comp", MODES)
+def test_persistent_blocks_share_arena_slots(mode, dtype, comp):
+    """R-MAT scale 14: thousands of long rows on fewer persistent blocks, each
+    reusing its arena slot for row after row; with an arena budget of one
+    byte a single block merges them all.  Same bits as the default run and as
+    the oracle on the largest rows."""
+    R = I.rmat(14, 16, seed=83)
+    C = run(R, R, "precise", dtype, comp, long_bucket=False)
+    same(C, run(R, R, "precise", dtype, comp, long_bucket=False, arena_bytes=1))
+    same(C, run(R, R, "upper", dtype, comp, long_bucket=False, arena_bytes=1 << 20))
+    nprod = oracle.row_nprod(R, R)
+    rows = np.sort(np.argsort(-nprod, kind="stable")[:40])
+    assert_rows_exact(C, oracle.alg1(R, R, rows, prec=mode), rows)
