@@ -154,8 +154,10 @@ typedef struct {
  *                  merge rounds -- persistent blocks, each holding one row's
  *                  buffers at a time -- or 1/8, at most 32 GiB, for the
  *                  column-bucket batches; always at least enough for the
- *                  longest row).  A smaller budget runs fewer persistent
- *                  blocks (merge rounds) or more batches (column buckets).
+ *                  longest row; BRMerge-Upper in row chunks: 1/8, at most
+ *                  32 GiB, per chunk).  A smaller budget runs fewer
+ *                  persistent blocks (merge rounds) or more batches (column
+ *                  buckets).
  *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
  *                  sizeof value) bytes) processed at once; a larger product
  *                  is processed in row chunks of at most this size, each

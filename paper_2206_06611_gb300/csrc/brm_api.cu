@@ -415,7 +415,8 @@ struct LongPlan {
     int32_t *ctr = nullptr;
 };
 
-int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp) {
+int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp,
+              bool persistent = true) {
     const int64_t nl = (int64_t)pl.long_rows_h.size();
     lp.starts.clear();
     if (nl == 0) return BRM_OK;
@@ -436,13 +437,14 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = (size_t)8 << 30; }
-        budget = lp.bucket ? std::min<size_t>(fr / 8, (size_t)32 << 30) : std::min<size_t>(fr / 4, (size_t)64 << 30);
+        budget = (lp.bucket || !persistent) ? std::min<size_t>(fr / 8, (size_t)32 << 30)
+                                            : std::min<size_t>(fr / 4, (size_t)64 << 30);
     }
     budget = std::max(budget, biggest);
     std::vector<int64_t> off(nl);
     size_t maxbatch = 0;
     lp.grid = 0;
-    if (!lp.bucket) {
+    if (!lp.bucket && persistent) {
         // merge rounds: the slots are sorted by product count, largest first.
         // Block b < R merges slot b and then slots R, R + 1, ... from a
         // counter; its arena holds max(need[b], the largest need after R).
@@ -506,7 +508,7 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
     int rc = get(mem, lp.off_d, nl, "arena offsets");
     if (rc) return rc;
     if ((rc = get(mem, lp.arena, maxbatch, "long-row arena"))) return rc;
-    if (!lp.bucket && (rc = get(mem, lp.ctr, 1, "long-row counter"))) return rc;
+    if (lp.grid > 0 && (rc = get(mem, lp.ctr, 1, "long-row counter"))) return rc;
     BRM_CUDA(cudaMemcpyAsync(lp.off_d, off.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
     return BRM_OK;
@@ -553,14 +555,15 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
 }
 
 // One BRMerge pass (symbolic or numeric) over all bins.
-int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j) {
+int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j, bool persistent = true) {
     LongPlan lp;
-    int rc = plan_long(mem, v, pl, o, j.bcols, lp);
+    int rc = plan_long(mem, v, pl, o, j.bcols, lp, persistent);
     if (rc) return rc;
     if ((rc = launch_pass(v, pl, lp, j, mem.st, true))) return rc;
     if (lp.arena) {
         mem.free_one(lp.arena);   // stream-ordered release after the launches
         mem.free_one(lp.off_d);
+        mem.free_one(lp.ctr);
     }
     return BRM_OK;
 }
@@ -757,7 +760,11 @@ int upper_chunked(Mem &mem, const brm_csr *A, const brm_csr *B, brm_csr_out *C, 
         j.out_val = cval;
         j.out_cnt = row_size + r0;
         j.err = err;
-        if ((rc = run_pass(mem, v, pc, o, j))) return rc;
+        // long rows in arena-sized batches of one block per row, an eighth of
+        // what is free at a time: the compacted chunks pile up to the size of
+        // C, and persistent blocks with a larger arena left the caller's
+        // allocator no room for C at the end (R-MAT scale 20)
+        if ((rc = run_pass(mem, v, pc, o, j, false))) return rc;
         {
             PhaseScope ps(kPhScan, mem.st);
             BRM_CUDA(launch_scan(row_size + r0, loc_rp, rows, tmp, mem.st));
