@@ -448,7 +448,8 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
         // merge rounds: the slots are sorted by product count, largest first.
         // Block b < R merges slot b and then slots R, R + 1, ... from a
         // counter; its arena holds max(need[b], the largest need after R).
-        // R is the resident block count, lowered until the arena fits.
+        // R is the resident block count (two 512-thread blocks of the arena
+        // kernel per SM), lowered until the arena fits the budget.
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
