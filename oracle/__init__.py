@@ -14,8 +14,9 @@ arrays.  Functions and what pins them (tests/test_oracle_*.py):
   3-D Laplacians, identity/permutation products and the transpose identity.
 * ``symbolic``   Section II-B's structural row counts.  Pinned by brute force
   and the Laplacian closed form.
-* ``alg1``       Algorithm 1 (Section III-B) step by step, double / float /
-  float with TwoSum.  Pinned by the Fig. 2 round count, a hand-derived case in
+* ``alg1``       the BRMerge accumulation (Section III-A/B, Algorithm 1,
+  Figs. 2-3): rounds that merge neighbouring lists until one is left, in
+  double / float / float with TwoSum.  Pinned by the Fig. 2 round count, a hand-derived case in
   which the tree order changes the double result, equality with Gustavson on
   integer inputs and the summation error bound elsewhere.
 * ``backward``   the gradients of sum(C * G).  Pinned by exact finite
@@ -190,19 +191,47 @@ def balanced_row_groups(nprod: np.ndarray, p: int):
     return np.maximum.accumulate(np.array(bounds, dtype=np.int64))
 
 
-def gustavson_parallel(A, B, threads: int, rows=None) -> Result:
-    """Gustavson on ``threads`` host threads over nprod-balanced row groups
-    (ctypes drops the GIL during each C call).  Same results as gustavson()."""
-    from concurrent.futures import ThreadPoolExecutor
-
+def _split_rows(A, B, rows, threads):
     rows = _rows(A, rows)
+    threads = max(1, min(int(threads or os.cpu_count() or 1), max(len(rows), 1)))
     bounds = balanced_row_groups(row_nprod(A, B, rows), threads)
-    parts = [rows[bounds[t]:bounds[t + 1]] for t in range(threads)]
-    with ThreadPoolExecutor(threads) as ex:
-        res = list(ex.map(lambda r: gustavson(A, B, r), parts))
+    return rows, bounds, [rows[bounds[t]:bounds[t + 1]] for t in range(threads)]
+
+
+def _join(rows, bounds, res) -> Result:
     crp = np.zeros(len(rows) + 1, dtype=np.int64)
     off = 0
     for t, r in enumerate(res):
         crp[bounds[t]:bounds[t + 1] + 1] = r.crp + off
         off += r.nnz
-    return Result(rows, crp, np.concatenate([r.col for r in res]), np.concatenate([r.val for r in res]))
+    cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0)  # noqa: E731
+    abs_ = cat([r.abs for r in res]) if all(r.abs is not None for r in res) else None
+    rounds = cat([r.rounds for r in res]).astype(np.int32) if all(r.rounds is not None for r in res) else None
+    return Result(rows, crp, cat([r.col for r in res]).astype(np.int32), cat([r.val for r in res]), abs_, rounds)
+
+
+def _pool_map(fn, parts):
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(len(parts)) as ex:
+        return list(ex.map(fn, parts))
+
+
+def gustavson_parallel(A, B, threads: int, rows=None, with_abs: bool = False) -> Result:
+    """Gustavson on ``threads`` host threads over nprod-balanced row groups
+    (ctypes drops the GIL during each C call).  Same results as gustavson()."""
+    rows, bounds, parts = _split_rows(A, B, rows, threads)
+    return _join(rows, bounds, _pool_map(lambda r: gustavson(A, B, r, with_abs), parts))
+
+
+def alg1_parallel(A, B, rows=None, prec: str = "f64", threads: int | None = None) -> Result:
+    """alg1() with the rows spread over host threads (each row is computed
+    by one call of the same single-threaded code; only the rows are split)."""
+    rows, bounds, parts = _split_rows(A, B, rows, threads)
+    return _join(rows, bounds, _pool_map(lambda r: alg1(A, B, r, prec), parts))
+
+
+def symbolic_parallel(A, B, rows=None, threads: int | None = None) -> np.ndarray:
+    """symbolic() with the rows spread over host threads."""
+    rows, bounds, parts = _split_rows(A, B, rows, threads)
+    res = _pool_map(lambda r: symbolic(A, B, r), parts)
+    return np.concatenate(res) if res else np.zeros(0, np.int64)

@@ -27,7 +27,8 @@
 /* ------------------------------------------------------------------------ */
 /* Intermediate-product count per output row:                                */
 /*   nprod_i = sum over k in A_i* of |B_k*|                                  */
-/* (Algorithm 1 line 1 and step 1 of both libraries, Section III-D).         */
+/* (step 1 of both allocation methods, Section III-D; the buffer sizing    */
+/* that opens Algorithm 1).                                                 */
 /* ------------------------------------------------------------------------ */
 void orc_row_nprod(int64_t nrows, const int64_t *rows,
                    const int32_t *arp, const int32_t *acol, const int32_t *brp,
@@ -133,32 +134,30 @@ int orc_gustavson(int64_t nrows, const int64_t *rows,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1 (BRMerge accumulation), taken step by step.                   */
+/* BRMerge accumulation (Section III-B, Fig. 2 and Fig. 3).                  */
 /*                                                                           */
-/* Multiplying phase: for each A_ik of the row, in stored order, the scaled  */
-/* row A_ik * B_k* is appended to the destination buffer and the list's end  */
-/* is recorded in the offset array -- also when B_k* is empty, so empty      */
-/* lists keep their place in the tree.                                       */
-/* Accumulating phase: while more than one list remains, lists are consumed  */
-/* two at a time in order (0,1), (2,3), ... and merged like a merge sort,    */
-/* adding the values of equal columns once; a last odd list is copied.  The  */
-/* buffers then swap roles.  The result row is in the source buffer.         */
-/* Section III-B, Fig. 2 (ceil(log2 L) rounds for L lists), Fig. 3.          */
-/*                                                                           */
-/* The buffers are allocated once for all rows from max_row_nprod_C and      */
-/* max_row_nnz_A (the algorithm's first line) and released at the end.       */
+/* Row i of C is built from the scaled rows A_ik * B_k* of its entries k, in */
+/* the stored order of A_i*.  Each scaled row is one sorted list; an empty   */
+/* B_k* gives an empty list that still takes its place in the sequence.      */
+/* The lists are then reduced in rounds: every round pairs neighbouring      */
+/* lists -- the 1st with the 2nd, the 3rd with the 4th, and so on -- and     */
+/* merges each pair like merge sort into one list, adding the values of a    */
+/* column present in both (the left list's value first); an unpaired last   */
+/* list goes to the next round as it is.  After ceil(log2 L) rounds one list */
+/* is left: the row of C.  Two scratch buffers take turns as the source and  */
+/* the destination of a round (the paper's ping-pong buffers).               */
 /*                                                                           */
 /* prec: 0 = double values; 1 = float values, float sums; 2 = float values   */
-/* with TwoSum-compensated merge additions.  In mode 2 every list element    */
-/* carries (s, e): a product starts as (a*b, 0); merging equal columns       */
-/* (x, y) gives s = x.s + y.s rounded, t its exact rounding error (Knuth's   */
-/* TwoSum), and e = (x.e + y.e) + t; the stored value is s + e.  Modes 1/2   */
-/* read avf/bvf and write float results, widened exactly, to cval.          */
-/* rounds_out (may be NULL) receives the number of merging rounds per row.   */
+/* with TwoSum-compensated additions.  In mode 2 every list element carries  */
+/* (s, e): a product starts as (a*b, 0); adding two elements (x, y) gives    */
+/* s = x.s + y.s rounded, t its exact rounding error (Knuth's TwoSum), and   */
+/* e = (x.e + y.e) + t; the stored value is s + e.  Modes 1/2 read avf/bvf   */
+/* and write float results, widened exactly, to cval.                        */
+/* rounds_out (may be NULL) receives the number of rounds of every row.      */
 /* ------------------------------------------------------------------------ */
 typedef struct { int32_t col; double v; float s; float e; } orc_elem;
 
-static orc_elem merge_equal(orc_elem x, orc_elem y, int prec)
+static orc_elem add_elems(orc_elem x, orc_elem y, int prec)
 {
     orc_elem r;
     r.col = x.col;
@@ -177,35 +176,66 @@ static orc_elem merge_equal(orc_elem x, orc_elem y, int prec)
     return r;
 }
 
+/* Merges the sorted lists x[0..nx) and y[0..ny) into out; returns the length. */
+static int64_t merge_pair(const orc_elem *x, int64_t nx, const orc_elem *y, int64_t ny, orc_elem *out, int prec)
+{
+    int64_t a = 0, b = 0, w = 0;
+    while (a < nx && b < ny) {
+        if (x[a].col < y[b].col) out[w++] = x[a++];
+        else if (y[b].col < x[a].col) out[w++] = y[b++];
+        else { out[w++] = add_elems(x[a], y[b], prec); ++a; ++b; }
+    }
+    while (a < nx) out[w++] = x[a++];
+    while (b < ny) out[w++] = y[b++];
+    return w;
+}
+
+/* One round: the n lists of src (list j is src[lo[j] .. lo[j+1])) become   */
+/* ceil(n/2) lists in dst, bounds in dlo.  Returns their number.             */
+static int64_t merge_round(const orc_elem *src, const int64_t *lo, int64_t n, orc_elem *dst, int64_t *dlo, int prec)
+{
+    int64_t m = 0;
+    dlo[0] = 0;
+    for (int64_t j = 0; j < n; j += 2) {
+        int64_t w = dlo[m];
+        if (j + 1 < n) {
+            w += merge_pair(src + lo[j], lo[j + 1] - lo[j], src + lo[j + 1], lo[j + 2] - lo[j + 1], dst + w, prec);
+        } else {
+            for (int64_t q = lo[j]; q < lo[j + 1]; ++q) dst[w++] = src[q];
+        }
+        dlo[++m] = w;
+    }
+    return m;
+}
+
 int orc_alg1(int64_t nrows, const int64_t *rows, int prec,
              const int32_t *arp, const int32_t *acol, const double *avd, const float *avf,
              const int32_t *brp, const int32_t *bcol, const double *bvd, const float *bvf,
              const int64_t *crp, int32_t *ccol, double *cval, int32_t *rounds_out)
 {
-    /* line 1: buffer sizes */
-    int64_t max_nprod = 0, max_nnz_a = 0;
+    /* scratch sized for the largest requested row: its products and lists */
+    int64_t most = 0, most_lists = 0;
     for (int64_t t = 0; t < nrows; ++t) {
         int64_t i = rows[t], s = 0;
         for (int32_t p = arp[i]; p < arp[i + 1]; ++p) s += brp[acol[p] + 1] - brp[acol[p]];
-        if (s > max_nprod) max_nprod = s;
-        if (arp[i + 1] - arp[i] > max_nnz_a) max_nnz_a = arp[i + 1] - arp[i];
+        if (s > most) most = s;
+        if (arp[i + 1] - arp[i] > most_lists) most_lists = arp[i + 1] - arp[i];
     }
-    /* lines 2-5: ping-pong buffers and their list offsets */
-    orc_elem *ping = (orc_elem *)malloc(sizeof(orc_elem) * (size_t)(max_nprod + 1));
-    orc_elem *pong = (orc_elem *)malloc(sizeof(orc_elem) * (size_t)(max_nprod + 1));
-    int64_t *ping_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(max_nnz_a + 1));
-    int64_t *pong_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(max_nnz_a + 1));
-    if (!ping || !pong || !ping_off || !pong_off) {
-        free(ping); free(pong); free(ping_off); free(pong_off); return -1;
+    orc_elem *buf[2];
+    int64_t *lo[2];
+    buf[0] = (orc_elem *)malloc(sizeof(orc_elem) * (size_t)(most + 1));
+    buf[1] = (orc_elem *)malloc(sizeof(orc_elem) * (size_t)(most + 1));
+    lo[0] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(most_lists + 2));
+    lo[1] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(most_lists + 2));
+    if (!buf[0] || !buf[1] || !lo[0] || !lo[1]) {
+        free(buf[0]); free(buf[1]); free(lo[0]); free(lo[1]); return -1;
     }
     int rc = 0;
     for (int64_t t = 0; t < nrows; ++t) {
         int64_t i = rows[t];
-        orc_elem *dst = ping;
-        int64_t *dst_off = ping_off;
-        int64_t buf_incr = 0, list_incr = 0;
-        dst_off[0] = 0;
-        /* multiplying phase */
+        /* the scaled rows A_ik * B_k*, one list per entry of A_i* */
+        int64_t n = 0, w = 0;
+        lo[0][0] = 0;
         for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
             int32_t k = acol[p];
             for (int32_t q = brp[k]; q < brp[k + 1]; ++q) {
@@ -214,60 +244,30 @@ int orc_alg1(int64_t nrows, const int64_t *rows, int prec,
                 e.v = 0.0; e.s = 0.0f; e.e = 0.0f;
                 if (prec == 0) e.v = avd[p] * bvd[q];
                 else e.s = avf[p] * bvf[q];
-                dst[buf_incr++] = e;
+                buf[0][w++] = e;
             }
-            dst_off[++list_incr] = buf_incr;
+            lo[0][++n] = w;
         }
-        int64_t num_list = list_incr;
-        orc_elem *src = dst;
-        int64_t *src_off = dst_off;
-        dst = pong;
-        dst_off = pong_off;
+        /* rounds until one list is left */
+        int cur = 0;
         int32_t rounds = 0;
-        /* accumulating phase */
-        while (num_list > 1) {
-            int64_t inner = num_list, li = 0, w = 0;
-            num_list = 0;
-            dst_off[0] = 0;
-            while (inner) {
-                if (inner >= 2) {
-                    /* consume lists li and li+1 */
-                    int64_t x = src_off[li], xe = src_off[li + 1];
-                    int64_t y = src_off[li + 1], ye = src_off[li + 2];
-                    while (x < xe && y < ye) {
-                        if (src[x].col < src[y].col) dst[w++] = src[x++];
-                        else if (src[y].col < src[x].col) dst[w++] = src[y++];
-                        else dst[w++] = merge_equal(src[x++], src[y++], prec);
-                    }
-                    while (x < xe) dst[w++] = src[x++];
-                    while (y < ye) dst[w++] = src[y++];
-                    li += 2;
-                    inner -= 2;
-                } else {
-                    /* copy the last list */
-                    for (int64_t x = src_off[li]; x < src_off[li + 1]; ++x) dst[w++] = src[x];
-                    li += 1;
-                    inner -= 1;
-                }
-                ++num_list;
-                dst_off[num_list] = w;
-            }
-            orc_elem *tb = src; src = dst; dst = tb;
-            int64_t *to = src_off; src_off = dst_off; dst_off = to;
+        while (n > 1) {
+            n = merge_round(buf[cur], lo[cur], n, buf[1 - cur], lo[1 - cur], prec);
+            cur = 1 - cur;
             ++rounds;
         }
-        /* store the row (the single remaining list, in src) */
-        int64_t len = (list_incr == 0) ? 0 : src_off[1];
+        int64_t len = n == 0 ? 0 : lo[cur][1];
         if (len != crp[t + 1] - crp[t]) { rc = -2; break; }
         for (int64_t s = 0; s < len; ++s) {
-            ccol[crp[t] + s] = src[s].col;
-            if (prec == 0) cval[crp[t] + s] = src[s].v;
-            else if (prec == 1) cval[crp[t] + s] = (double)src[s].s;
-            else cval[crp[t] + s] = (double)(float)(src[s].s + src[s].e);
+            const orc_elem *e = &buf[cur][s];
+            ccol[crp[t] + s] = e->col;
+            if (prec == 0) cval[crp[t] + s] = e->v;
+            else if (prec == 1) cval[crp[t] + s] = (double)e->s;
+            else cval[crp[t] + s] = (double)(float)(e->s + e->e);
         }
         if (rounds_out) rounds_out[t] = rounds;
     }
-    free(ping); free(pong); free(ping_off); free(pong_off);
+    free(buf[0]); free(buf[1]); free(lo[0]); free(lo[1]);
     return rc;
 }
 

@@ -394,6 +394,18 @@ def test_parallel_gustavson_matches():
     assert np.array_equal(r1.crp, r2.crp) and np.array_equal(r1.col, r2.col) and np.array_equal(r1.val, r2.val)
 
 
+def test_parallel_alg1_and_symbolic_match():
+    """Spreading rows over threads changes nothing: same rows, same values,
+    in the requested row order (also for an unsorted sample)."""
+    A = I.rmat(10, 8, seed=5)
+    rows = np.array([1000, 3, 3, 0, 511, 17, 1023], dtype=np.int64)
+    for prec in ("f64", "f32c"):
+        r1, r2 = oracle.alg1(A, A, rows, prec), oracle.alg1_parallel(A, A, rows, prec, threads=3)
+        assert np.array_equal(r1.crp, r2.crp) and np.array_equal(r1.col, r2.col)
+        assert np.array_equal(r1.val, r2.val) and np.array_equal(r1.rounds, r2.rounds)
+    assert np.array_equal(oracle.symbolic(A, A), oracle.symbolic_parallel(A, A, threads=4))
+
+
 def test_sampled_rows_match_full():
     A = I.rmat(10, 8, seed=6)
     full = oracle.alg1(A, A)
