@@ -1,22 +1,27 @@
 """Benchmark of BRMerge SpGEMM on one GB300 (or N, one independent product per GPU).
 
-Workload: C = A*A, A Erdos-Renyi with n = 2^20 rows and exactly 16 distinct
-uniform columns per row, FP64 values U[-1,1), seeded (synthetic; the paper's
-SuiteSparse matrices are not used).  One step = one whole BRMerge-Precise call
-(product counts + binning, symbolic pass, prefix sum, allocation of C,
-numeric pass) on inputs already resident in HBM.  The inputs (A: 205 MB) and
-the output (C: 3.2 GB) are both larger than the 129 MB L2, so no explicit L2
-flush is needed between steps.
+Headline workload: C = A*A, A the R-MAT graph of scale 20 (n = 2^20, edge
+factor 16, quadrant probabilities (0.57, 0.19, 0.19, 0.05), duplicates
+removed), FP64 values U[-1,1), seeded (synthetic: the paper's SuiteSparse
+matrices are not used).  It is the largest configuration that runs on one
+GPU: ~20.9e9 intermediate products, nnz(C) ~9.7e9, C ~116 GB.  One step is one
+whole BRMerge-Precise call (product counts + binning, symbolic pass, prefix
+sum, allocation of C, numeric pass) on inputs already resident in HBM.  The
+output (116 GB) is far larger than the 129 MB L2, so no explicit L2 flush is
+needed between steps.
 
 Metric (the paper's, Section IV-A): GFLOP/s = 2 * intermediate products / s.
 
-Printed: one JSON line with value (device-timed, all ranks), e2e (through the
-same C-ABI call with host buffers: A copied in from pinned host memory and C
-copied back every step), the roofline of the dominant kernel (the numeric
-kernel of the busiest bin -- for this workload the register bin of 8 threads
-per row -- timed live with CUDA events recorded by the library on its launch
-stream), clocks sampled with nvidia-smi during the timed region, and a
-cpu_baseline (the CPU oracle on a bounded sample of rows).
+Printed: one JSON line with the value (device-timed, all ranks), e2e (the
+same call with host buffers: A copied in from pinned host memory and all of
+C copied back every step), the roofline of the dominant kernel (the numeric
+pass of the long rows, timed live with CUDA events that the library records
+on its launch stream), clocks sampled with nvidia-smi during the timed
+region, a cpu_baseline (the CPU oracle on a bounded sample of rows, on all
+host cores and on one), and under "also" the other configurations measured in
+the same run: the Erdos-Renyi product, the FP32 and FP32+TwoSum paths of the
+R-MAT product with their error against the FP64 oracle, the 512-product batch
+against 512 single calls, and the differentiable form's forward and backward.
 
 ``--impl reference`` times the CPU oracle itself (the only reference that
 exists for this method) on bounded samples of the same workload.
@@ -26,6 +31,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -41,13 +47,24 @@ from paper_2206_06611_gb300 import inputs as I  # noqa: E402
 
 METRIC = "SpGEMM GFLOP/s (2*products/s)"
 UNIT = "GFLOP/s"
-WORKLOAD = "ER n=2^20, 16 nnz/row, C=A*A, FP64, BRMerge-Precise"
 
-# DRAM bytes (read + write) of one launch of the dominant kernel (the numeric
-# register-bin kernel on this workload), from an ncu capture of the current
-# kernel source (dram__bytes_read.sum + dram__bytes_write.sum); set to None
-# whenever that kernel changes until it is captured again.
-NUMERIC_REG_TRAFFIC = 3.898992e9 + 3.184545e9
+# Row bins of the default options (include/brm.h): rows with more than this
+# many products, or more lists, are the long rows.
+BLOCK_MAX_NPROD = 4096
+BLOCK_MAX_L = 1024
+
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
+# capture of the current source of that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, scaled to one full launch as the profile says), or
+# None when the kernel changed after the capture.
+TRAFFIC = {"numeric_long": None, "numeric_reg": None}
+
+
+def workload_name(scale: int) -> str:
+    return f"R-MAT scale {scale} ef16 (0.57,0.19,0.19,0.05) dedup, C=A*A, FP64, BRMerge-Precise"
+
+
+ER_WORKLOAD = "ER n=2^20, 16 nnz/row, C=A*A, FP64, BRMerge-Precise"
 
 
 def peaks():
@@ -57,6 +74,24 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 def reduce_max(x: float, dist, device) -> float:
@@ -87,6 +122,13 @@ def dist_env():
     return rank, world, local
 
 
+def check_world(args, world: int):
+    """--gpus must agree with the launch: N > 1 runs under torchrun with N ranks."""
+    if args.gpus != world:
+        raise SystemExit(f"--gpus {args.gpus} but {world} rank(s) were launched; run N > 1 as "
+                         f"python -m torch.distributed.run --nproc-per-node {args.gpus} bench.py --gpus {args.gpus}")
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -100,7 +142,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(dev_index)], stdout=self.f,
+                                          "-lms", "100", "-i", str(dev_index)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -108,7 +150,7 @@ class Clocks:
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -135,77 +177,163 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes of the numeric pass (compulsory traffic, per launch)
+# algorithmic bytes (compulsory traffic) of the numeric pass over some rows
 # ---------------------------------------------------------------------------
-def numeric_bytes(A, B, nnz_c, vbytes):
-    """A once (row_ptr, col, val), the B rows A touches once, C.row_ptr read
-    once and C's columns and values written once."""
-    touched = np.zeros(B.rows, dtype=bool)
-    touched[A.col] = True
+def numeric_bytes(A, B, rows_mask, row_nnz_c, vbytes):
+    """A's rows once (row_ptr entries, columns, values), the B rows they name
+    once (two row_ptr entries, columns, values), C's row_ptr entries read and
+    its columns and values written once -- for the rows in rows_mask."""
+    alen = np.diff(A.rp.astype(np.int64))
     blen = np.diff(B.rp.astype(np.int64))
+    rows = np.nonzero(rows_mask)[0]
+    ents = np.repeat(rows_mask, alen)
+    touched = np.zeros(B.rows, dtype=bool)
+    touched[A.col[ents]] = True
+    a_bytes = len(rows) * 4 + int(alen[rows].sum()) * (4 + vbytes)
     b_bytes = int(touched.sum()) * 2 * 4 + int(blen[touched].sum()) * (4 + vbytes)
-    a_bytes = (A.rows + 1) * 4 + A.nnz * (4 + vbytes)
-    c_bytes = (A.rows + 1) * 8 + nnz_c * (4 + vbytes)
+    c_bytes = len(rows) * 8 + int(row_nnz_c[rows].sum()) * (4 + vbytes)
     return a_bytes + b_bytes + c_bytes
+
+
+def long_rows_mask(A, nprod):
+    L = np.diff(A.rp.astype(np.int64))
+    return (nprod > 0) & ((nprod > BLOCK_MAX_NPROD) | (L > BLOCK_MAX_L))
+
+
+def roofline(trace, phase, alg_bytes, traffic_key):
+    k_ms, k_launch = trace.get(phase, (0.0, 0))
+    if not k_launch:
+        return None
+    per_launch_ms = k_ms / k_launch
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": phase, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": TRAFFIC.get(traffic_key),
+            "algorithmic_bytes": alg_bytes, "kernel_ms": per_launch_ms, "launches_per_step": k_launch}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(A, target_s: float, threads: int):
-    """Time the oracle's Gustavson (row-parallel over nprod-balanced groups)
-    on the first rows of A*A, enough for about target_s seconds."""
+def sample_rows(nprod, budget_products: int, seed: int):
+    """Seeded random rows (without replacement, in increasing order) whose
+    products add up to about budget_products."""
+    order = np.argsort(I.rand_u64(seed, 77, np.arange(len(nprod))), kind="stable")
+    cum = np.cumsum(nprod[order])
+    k = int(np.searchsorted(cum, budget_products)) + 1
+    return np.sort(order[:max(1, min(k, len(order)))]).astype(np.int64)
+
+
+def oracle_rate(A, nprod, target_s: float, threads: int, seed: int):
+    """GFLOP/s of the oracle's Gustavson (row-parallel over nprod-balanced
+    groups) on a seeded row sample sized for about target_s seconds."""
     import oracle
     oracle.build()
-    nprod = oracle.row_nprod(A, A)
-    # calibrate on a small slice
-    rows = np.arange(min(A.rows, 20000), dtype=np.int64)
+    rows = sample_rows(nprod, int(2e6) * threads, seed)
+    t0 = time.perf_counter()
+    oracle.gustavson_parallel(A, A, threads, rows)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = nprod[rows].sum() / dt
+    rows = sample_rows(nprod, int(rate * target_s), seed + 1)
     t0 = time.perf_counter()
     oracle.gustavson_parallel(A, A, threads, rows)
     dt = time.perf_counter() - t0
-    rate = nprod[rows].sum() / max(dt, 1e-6)
-    want = int(min(A.rows, max(len(rows), rate * target_s / max(nprod.mean(), 1))))
-    rows = np.arange(want, dtype=np.int64)
-    t0 = time.perf_counter()
-    oracle.gustavson_parallel(A, A, threads, rows)
-    dt = time.perf_counter() - t0
-    flops = 2.0 * float(nprod[rows].sum())
-    return flops / dt / 1e9, dt, want
+    return 2.0 * float(nprod[rows].sum()) / dt / 1e9, dt, len(rows), int(nprod[rows].sum())
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    A = I.erdos_renyi(1 << 20, 16)
+    import oracle
+    A = I.rmat(args.scale, 16)
+    nprod = oracle.row_nprod(A, A)
     threads = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        oracle_sample(A, 2.0, threads)
-    vals, secs, rows = [], [], 0
-    for _ in range(args.steps):
-        v, dt, rows = oracle_sample(A, 8.0, threads)
+    for w in range(args.warmup):
+        oracle_rate(A, nprod, 1.0, threads, 1000 + w)
+    vals, secs, info = [], [], None
+    for s in range(args.steps):
+        v, dt, nrows, npr = oracle_rate(A, nprod, 6.0, threads, 2000 + s)
         vals.append(v)
         secs.append(dt)
+        info = (nrows, npr)
     value = float(np.mean(vals))
-    sample = f"first {rows} of {A.rows} rows of A*A per step (Gustavson, FP64)"
+    sample = (f"per step ~{info[0]} seeded random rows of {A.rows} ({info[1]:.3g} of {int(nprod.sum()):.3g} "
+              f"products) of A*A, Gustavson FP64 on {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "cpu oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(args.scale), "n": A.rows, "nnz_A": A.nnz, "nprod": int(nprod.sum()),
+                   "global_batch": 1, "parallelism": "cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 # ---------------------------------------------------------------------------
-# GPU arm
+# timing helpers
+# ---------------------------------------------------------------------------
+def _timed(fn, steps, warmup):
+    """Milliseconds per call of fn (CUDA events on the current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _traced(fn, steps, warmup):
+    """(ms per call, {phase: (ms per call, launches per call)})."""
+    from paper_2206_06611_gb300 import brm
+    for _ in range(warmup):
+        fn()
+    brm.brm_trace_reset()
+    brm.brm_trace_enable(True)
+    ms = _timed(fn, steps, 0)
+    t = brm.brm_trace_read()
+    brm.brm_trace_enable(False)
+    return ms, {k: (v[0] / steps, v[1] / steps) for k, v in t.items() if v[1]}
+
+
+def _rows_to_host(C, rows):
+    """(row_ptr, col, val) of the given rows of a device result."""
+    import torch
+    rp = C.rp.cpu().numpy()
+    starts, ends = rp[rows], rp[rows + 1]
+    idx = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]) if len(rows) else np.zeros(0, np.int64)
+    it = torch.from_numpy(idx).to(C.col.device)
+    crp = np.zeros(len(rows) + 1, dtype=np.int64)
+    crp[1:] = np.cumsum(ends - starts)
+    return crp, C.col[it].cpu().numpy(), C.val[it].cpu().numpy().astype(np.float64)
+
+
+def _row_err(crp, val, ref):
+    d = (val - ref.val) ** 2
+    cs, ca = np.concatenate(([0.0], np.cumsum(d))), np.concatenate(([0.0], np.cumsum(ref.abs ** 2)))
+    num = np.sqrt(np.maximum(cs[crp[1:]] - cs[crp[:-1]], 0))
+    den = np.sqrt(np.maximum(ca[crp[1:]] - ca[crp[:-1]], 0))
+    return np.where(den > 0, num / np.where(den > 0, den, 1), 0)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm: the headline line
 # ---------------------------------------------------------------------------
 def run_gpu(args):
     import torch
     from paper_2206_06611_gb300 import brm
+    import oracle
 
     rank, world, local = dist_env()
+    check_world(args, world)
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -221,19 +349,29 @@ def run_gpu(args):
             dist.barrier()
 
     # every rank multiplies its own independent matrix (weak scaling)
-    A = I.erdos_renyi(1 << 20, 16, seed=rank_seed(rank))
+    if args.workload == "er":
+        A = I.erdos_renyi(1 << 20, 16, seed=rank_seed(rank))
+        wname = ER_WORKLOAD
+        phase = "numeric_reg"
+    else:
+        A = I.rmat(args.scale, 16, seed=rank_seed(rank))
+        wname = workload_name(args.scale)
+        phase = "numeric_long"
     vbytes = 8
+    nprod = oracle.row_nprod(A, A)
+    nprod_total = int(nprod.sum())
     dA = brm.to_device(A, device=f"cuda:{dev}")
     st = torch.cuda.current_stream()
 
-    # warm-up (also gives the result size)
+    # warm-up (also gives the result's row lengths)
     C = None
     for _ in range(args.warmup):
         C = brm.brm_spgemm_precise(dA, dA)
     torch.cuda.synchronize()
+    row_nnz = np.diff(C.rp.cpu().numpy())
     nnz_c = C.nnz
     del C
-    nprod_total = brm.brm_row_nprod(dA, dA)[1]
+    torch.cuda.empty_cache()
 
     # ---- device-resident timed region --------------------------------------
     clocks = Clocks(dev) if rank == 0 else None
@@ -259,29 +397,38 @@ def run_gpu(args):
     value = job_gflops(nprod_total, world, args.steps, ms_max)
 
     # ---- end to end: host buffers, copies inside the timed region ----------
+    # A comes in from pinned host memory every step; all of C goes back to
+    # the host every step, through two pinned staging buffers used in turn
+    # (C is larger than is sensible to pin at once).
     hA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
           for k, v in (("rp", A.rp.astype(np.int32)), ("col", A.col.astype(np.int32)), ("val", A.val))}
     h2d = sum(t.numel() * t.element_size() for t in hA.values())
-    out_rp = torch.empty(A.rows + 1, dtype=torch.int64).pin_memory()
-    out_col = torch.empty(nnz_c, dtype=torch.int32).pin_memory()
-    out_val = torch.empty(nnz_c, dtype=torch.float64).pin_memory()
-    d2h = out_rp.numel() * 8 + nnz_c * (4 + vbytes)
+    stage_bytes = 1 << 30
+    stages = [torch.empty(stage_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    d2h = (A.rows + 1) * 8 + nnz_c * (4 + vbytes)
     dA2 = brm.DeviceCSR(A.rows, A.cols, torch.empty_like(dA.rp), torch.empty_like(dA.col), torch.empty_like(dA.val))
-    e_steps = max(1, min(args.steps, 5))
+
+    def copy_out(t, k):
+        b = t.view(torch.uint8).reshape(-1)
+        for o in range(0, b.numel(), stage_bytes):
+            n = min(stage_bytes, b.numel() - o)
+            stages[k % 2][:n].copy_(b[o:o + n], non_blocking=True)
+            k += 1
+        return k
+
+    e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(st)
     for _ in range(e_steps):
         dA2.rp.copy_(hA["rp"], non_blocking=True)
         dA2.col.copy_(hA["col"], non_blocking=True)
         dA2.val.copy_(hA["val"], non_blocking=True)
         C = brm.brm_spgemm_precise(dA2, dA2)
-        out_rp.copy_(C.rp, non_blocking=True)
-        out_col.copy_(C.col, non_blocking=True)
-        out_val.copy_(C.val, non_blocking=True)
+        k = copy_out(C.rp, 0)
+        k = copy_out(C.col, k)
+        copy_out(C.val, k)
         del C
     f1.record(st)
     torch.cuda.synchronize()
@@ -289,6 +436,8 @@ def run_gpu(args):
     barrier()
     e2e_ms = reduce_max(e2e_ms, dist, f"cuda:{dev}")
     e2e_value = job_gflops(nprod_total, world, e_steps, e2e_ms)
+    del stages, hA, dA2
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
@@ -296,54 +445,230 @@ def run_gpu(args):
         return
 
     # ---- roofline of the dominant kernel ------------------------------------
-    kern = max(("numeric_reg", "numeric_warp", "numeric_block", "numeric_long"), key=lambda k: trace[k][0])
-    k_ms, k_launch = trace[kern]
-    per_launch_ms = k_ms / max(k_launch, 1)
-    alg_bytes = numeric_bytes(A, A, nnz_c, vbytes) if kern.startswith("numeric") else None
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if alg_bytes else None
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
-                "traffic": NUMERIC_REG_TRAFFIC if kern == "numeric_reg" else None,
-                "algorithmic_bytes": alg_bytes, "kernel_ms": per_launch_ms}
-    phases = {k: round(v[0] / args.steps, 4) for k, v in trace.items() if v[1]}
+    if phase == "numeric_long":
+        mask = long_rows_mask(A, nprod)
+    else:
+        L = np.diff(A.rp.astype(np.int64))
+        mask = (nprod > 0) & (nprod <= 1024) & (L <= 256)
+    per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in trace.items() if v[1]}
+    roof = roofline(per_step, phase, numeric_bytes(A, A, mask, row_nnz, vbytes), phase)
+    phases = {k: round(v[0], 4) for k, v in per_step.items()}
 
-    # ---- CPU oracle on a bounded sample --------------------------------------
+    # ---- CPU oracle on bounded samples ---------------------------------------
     cpu = None
     if not args.no_cpu and world == 1:
         threads = os.cpu_count() or 1
-        v, dt, rows = oracle_sample(A, args.cpu_seconds, threads)
+        v, dt, nrows, npr = oracle_rate(A, nprod, args.cpu_seconds, threads, 11)
+        v1, dt1, nrows1, npr1 = oracle_rate(A, nprod, args.cpu_seconds / 3, 1, 12)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {rows} of {A.rows} rows of A*A (Gustavson FP64, {dt:.1f} s)"}
+               "sample": f"{nrows} seeded random rows of {A.rows} ({npr:.3g} products) of A*A, Gustavson FP64, "
+                         f"{dt:.1f} s on {threads} threads",
+               "value_1core": v1,
+               "sample_1core": f"{nrows1} seeded random rows ({npr1:.3g} products), {dt1:.1f} s on 1 thread",
+               "cpu_model": cpu_model()}
 
-    print(json.dumps({
+    line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": A.rows, "nnz_A": A.nnz, "nprod": nprod_total, "nnz_C": nnz_c,
+        "config": {"workload": wname, "n": A.rows, "nnz_A": A.nnz, "nprod": nprod_total, "nnz_C": nnz_c,
                    "global_batch": world, "parallelism": f"independent products x{world}",
-                   "l2": "inputs (205 MB) and output (3.2 GB) exceed L2; no flush"},
+                   "l2": "output larger than L2 every step; no flush"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e_steps},
         "gpu_launches": launches,
-        "roofline": roofline,
+        "roofline": roof,
         "phases_ms_per_step": phases,
         "clocks": clk,
         "cpu_baseline": cpu,
-    }), flush=True)
+    }
+    if world == 1 and not args.headline_only:
+        also = {}
+        if args.workload != "er":
+            also["er"] = _guard(extra_er, args)
+            also["rmat_precision"] = _guard(extra_rmat_precision, args, A, nprod, ms_max / args.steps)
+        also["batched"] = _guard(extra_batched, args)
+        also["differentiable"] = _guard(extra_diff, args)
+        line["also"] = also
+    print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
+def _guard(fn, *a):
+    import torch
+    try:
+        return fn(*a)
+    except Exception as e:  # a failing extra must not hide the headline
+        return {"error": f"{type(e).__name__}: {e}"}
+    finally:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# the other configurations (the "also" block)
+# ---------------------------------------------------------------------------
+def extra_er(args):
+    """Erdos-Renyi n = 2^20, 16 per row: GFLOP/s and the numeric register
+    kernel's roofline."""
+    from paper_2206_06611_gb300 import brm
+    import oracle
+    A = I.erdos_renyi(1 << 20, 16)
+    nprod = oracle.row_nprod(A, A)
+    dA = brm.to_device(A)
+    C = brm.brm_spgemm_precise(dA, dA)
+    row_nnz = np.diff(C.rp.cpu().numpy())
+    del C
+    ms, tr = _traced(lambda: brm.brm_spgemm_precise(dA, dA), max(args.steps, 20), 3)
+    L = np.diff(A.rp.astype(np.int64))
+    mask = (nprod > 0) & (nprod <= 1024) & (L <= 256)
+    return {"workload": ER_WORKLOAD, "ms_per_step": ms, "gflops": 2.0 * nprod.sum() / (ms * 1e-3) / 1e9,
+            "roofline": roofline(tr, "numeric_reg", numeric_bytes(A, A, mask, row_nnz, 8), "numeric_reg"),
+            "phases_ms": {k: round(v[0], 4) for k, v in tr.items()}}
+
+
+def extra_rmat_precision(args, A, nprod, ms_f64):
+    """The same R-MAT product with FP32 values, plain and TwoSum-compensated:
+    time, speedup over the FP64 headline, and per-row error (normwise, scaled
+    by |A||B|) against the FP64 oracle on 400 sampled rows, the 100 longest
+    among them."""
+    import torch
+    from paper_2206_06611_gb300 import brm
+    import oracle
+    top = np.argsort(-nprod, kind="stable")[:100]
+    rows = np.unique(np.concatenate([top, I.rand_below(17, 30, np.arange(300), A.rows)]))
+    Af = A.astype(np.float32)
+    A64 = I.CSR(A.rows, A.cols, A.rp, A.col, Af.val.astype(np.float64))
+    ref = oracle.gustavson_parallel(A64, A64, os.cpu_count() or 1, rows, with_abs=True)
+    out = {}
+    for name, comp in (("f32", False), ("f32_twosum", True)):
+        dA = brm.to_device(Af)
+        C = brm.brm_spgemm_precise(dA, dA, compensated=comp)
+        crp, col, val = _rows_to_host(C, rows)
+        assert np.array_equal(col, ref.col), "structure differs from the oracle"
+        err = _row_err(crp, val, ref)
+        del C
+        torch.cuda.empty_cache()
+        steps = max(2, min(args.steps, 5))
+        ms, tr = _traced(lambda: brm.brm_spgemm_precise(dA, dA, compensated=comp), steps, 1)
+        out[name] = {"ms_per_step": ms, "gflops": 2.0 * nprod.sum() / (ms * 1e-3) / 1e9,
+                     "speedup_vs_f64": ms_f64 / ms,
+                     "row_err_vs_f64_oracle": {"max": float(err.max()), "median": float(np.median(err)),
+                                               "rows": int(len(rows))},
+                     "phases_ms": {k: round(v[0], 3) for k, v in tr.items()}}
+        del dA
+        torch.cuda.empty_cache()
+    return out
+
+
+def extra_batched(args):
+    """512 uneven products: one batched call vs 512 single calls, the numeric
+    pass replayed from a CUDA graph, autotuned bins; FP64 and FP32."""
+    import torch
+    from paper_2206_06611_gb300 import brm
+    import oracle
+    out = {"workload": "batched: 512 products A_i*A_i, n_i log-uniform in [1e3, 2e5], half 3-D Laplacian, "
+                       "half ER with 4..32 per row"}
+    mats64 = I.batched_mix(512)
+    total = int(sum(oracle.row_nprod(M, M).sum() for M in mats64))
+    for name, dtype in (("f64", np.float64), ("f32", np.float32)):
+        dev = [brm.to_device(M.astype(dtype)) for M in mats64]
+        gf = lambda ms: 2.0 * total / (ms * 1e-3) / 1e9  # noqa: E731
+
+        def batched():
+            C, _ = brm.brm_spgemm_batched(dev, dev)
+            del C
+
+        def separate():
+            for d in dev:
+                C = brm.brm_spgemm_precise(d, d)
+                del C
+
+        r = {"nprod": total}
+        r["separate_ms"] = _timed(separate, 3, 1)
+        r["batched_ms"] = _timed(batched, 5, 2)
+        opts, tune_ms = brm.brm_autotune(dev, dev)
+        r["autotuned"] = {k: opts[k] for k in ("reg_keys", "reg_warps", "warp_max_nprod", "block_max_nprod",
+                                                "reg_max_nprod")}
+        r["autotune_best_ms"] = tune_ms
+
+        def batched_tuned():
+            C, _ = brm.brm_spgemm_batched(dev, dev, **opts)
+            del C
+
+        r["batched_tuned_ms"] = _timed(batched_tuned, 5, 2)
+        b = brm.Batch(dev, dev, **opts)
+        r["numeric_graph_ms"] = _timed(b.graph_launch, 5, 2)
+        r["numeric_launch_ms"] = _timed(b.numeric, 5, 2)
+        b.check()
+        b.close()
+        for k in ("separate_ms", "batched_ms", "batched_tuned_ms"):
+            r[k.replace("_ms", "_gflops")] = gf(r[k])
+        r["speedup_batched_vs_separate"] = r["separate_ms"] / r["batched_tuned_ms"]
+        out[name] = r
+        del dev
+        torch.cuda.empty_cache()
+    return out
+
+
+def extra_diff(args):
+    """Differentiable C = A*B (A R-MAT scale 18 ef16, B ER 2^18 with 8 per row,
+    FP32 N(0,1)): forward, hand-written backward, and the FP64 plain forward."""
+    import torch
+    from paper_2206_06611_gb300 import brm
+    import oracle
+    A = I.normal_values(I.rmat(18, 16), 101)
+    B = I.normal_values(I.erdos_renyi(1 << 18, 8), 102)
+    total = int(oracle.row_nprod(A, B).sum())
+    dA, dB = brm.to_device(A), brm.to_device(B)
+    a_val = dA.val.clone().requires_grad_(True)
+    b_val = dB.val.clone().requires_grad_(True)
+    Aq = brm.DeviceCSR(A.rows, A.cols, dA.rp, dA.col, a_val)
+    Bq = brm.DeviceCSR(B.rows, B.cols, dB.rp, dB.col, b_val)
+    C = brm.spgemm(Aq, Bq)
+    G = torch.from_numpy(I.rand_normal(103, I.S_GRAD, np.arange(C.nnz)).astype(np.float32)).cuda()
+    Cd = brm.DeviceCSR(C.rows, C.cols, C.rp, C.col, None)
+    del C
+
+    def fwd():
+        Cx = brm.spgemm(Aq, Bq)
+        del Cx
+
+    def fwd_bwd():
+        Cx = brm.spgemm(Aq, Bq)
+        (Cx.val * G).sum().backward()
+        a_val.grad = None
+        b_val.grad = None
+
+    def bwd_only():
+        brm.brm_spgemm_backward(dA, dB, Cd, G)
+
+    d64A, d64B = brm.to_device(A.astype(np.float64)), brm.to_device(B.astype(np.float64))
+
+    def fwd64():
+        Cx = brm.brm_spgemm_precise(d64A, d64B)
+        del Cx
+
+    steps = max(args.steps, 10)
+    out = {"workload": "differentiable C=A*B, A R-MAT scale 18 ef16, B ER 2^18 8/row, FP32 N(0,1)", "nprod": total}
+    out["fwd_f32_ms"] = _timed(fwd, steps, 3)
+    out["bwd_f32_ms"] = _timed(bwd_only, steps, 3)
+    out["fwd_bwd_f32_ms"] = _timed(fwd_bwd, steps, 3)
+    out["fwd_f64_plain_ms"] = _timed(fwd64, steps, 3)
+    out["speedup_f32_fwd_vs_f64_plain"] = out["fwd_f64_plain_ms"] / out["fwd_f32_ms"]
+    out["fwd_f32_gflops"] = 2.0 * total / (out["fwd_f32_ms"] * 1e-3) / 1e9
+    return out
+
+
+# ---------------------------------------------------------------------------
+# fixed call sequences for ncu captures (no timing)
+# ---------------------------------------------------------------------------
 def run_profile(args):
-    """A short fixed sequence of calls for ncu to capture (no timing):
-    er       two BRMerge-Precise calls on the ER workload (n = --profile-n);
+    """er       two BRMerge-Precise calls on the ER workload (n = --profile-n);
     rmat     two BRMerge-Precise calls on R-MAT of scale --scale;
-             er and rmat take the long rows' numeric pass by column buckets
-             with --long-bucket;
-    batched  a prepared batch of the product mix (--batch-count products,
-             512 by default), its numeric pass twice, then one
-             brm_spgemm_batched call;
+    batched  a prepared batch of the product mix (--batch-count products),
+             its numeric pass twice, then one brm_spgemm_batched call;
     diff     the differentiable workload's forward and backward once each."""
     import torch
     from paper_2206_06611_gb300 import brm
@@ -380,229 +705,6 @@ def run_profile(args):
     print(json.dumps(info), flush=True)
 
 
-# ---------------------------------------------------------------------------
-# the other configurations (reported beside the headline line)
-# ---------------------------------------------------------------------------
-def _timed(fn, steps, warmup):
-    """Milliseconds per call of fn (CUDA events on the current stream)."""
-    import torch
-    for _ in range(warmup):
-        fn()
-    torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(steps):
-        fn()
-    e1.record(st)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps
-
-
-def _sample_rows(nprod, count, seed):
-    top = np.argsort(-nprod, kind="stable")[: count // 4]
-    rnd = I.rand_below(seed, 30, np.arange(count), len(nprod))
-    return np.unique(np.concatenate([top, rnd]))
-
-
-def _rows_to_host(C, rows):
-    """(row_ptr, col, val) of the given rows of a device result."""
-    import torch
-    rp = C.rp.cpu().numpy()
-    starts, ends = rp[rows], rp[rows + 1]
-    idx = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]) if len(rows) else np.zeros(0, np.int64)
-    it = torch.from_numpy(idx).to(C.col.device)
-    crp = np.zeros(len(rows) + 1, dtype=np.int64)
-    crp[1:] = np.cumsum(ends - starts)
-    return crp, C.col[it].cpu().numpy(), C.val[it].cpu().numpy().astype(np.float64)
-
-
-def run_rmat(args):
-    """R-MAT A*A: FP64 plain, FP32 plain and FP32 with TwoSum; GFLOP/s and the
-    FP32 error against the FP64 oracle on sampled rows."""
-    import torch
-    import oracle
-    from paper_2206_06611_gb300 import brm
-    torch.cuda.set_device(0)
-    A = I.rmat(args.scale, 16)
-    nprod = oracle.row_nprod(A, A)
-    total = int(nprod.sum())
-    rows = _sample_rows(nprod, 400, 17)
-    ref = oracle.gustavson(A, A, rows, with_abs=True)
-    out = {"workload": f"R-MAT scale {args.scale} ef16 dedup, C=A*A, BRMerge-Precise", "n": A.rows, "nnz_A": A.nnz,
-           "nprod": total}
-    for mode, dtype, comp in (("f64", np.float64, False), ("f32", np.float32, False), ("f32_twosum", np.float32, True)):
-        dA = brm.to_device(A, dtype=dtype)
-        C = brm.brm_spgemm_precise(dA, dA, compensated=comp)
-        torch.cuda.synchronize()
-        crp, col, val = _rows_to_host(C, rows)
-        assert np.array_equal(col, ref.col), "structure differs from the oracle"
-        d = (val - ref.val) ** 2
-        cs, ca = np.concatenate(([0.0], np.cumsum(d))), np.concatenate(([0.0], np.cumsum(ref.abs ** 2)))
-        num = np.sqrt(np.maximum(cs[crp[1:]] - cs[crp[:-1]], 0))
-        den = np.sqrt(np.maximum(ca[crp[1:]] - ca[crp[:-1]], 0))
-        err = np.where(den > 0, num / np.where(den > 0, den, 1), 0)
-        nnz_c = C.nnz
-        del C
-        torch.cuda.empty_cache()
-
-        def step():
-            Cx = brm.brm_spgemm_precise(dA, dA, compensated=comp)
-            del Cx
-
-        brm.brm_trace_reset()
-        brm.brm_trace_enable(True)
-        ms = _timed(step, args.steps, max(1, min(args.warmup, 2)))
-        t = brm.brm_trace_read()
-        brm.brm_trace_enable(False)
-        n_calls = args.steps + max(1, min(args.warmup, 2))
-        out[mode] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9, "nnz_C": nnz_c,
-                     "phases_ms": {k: round(v[0] / n_calls, 3) for k, v in t.items() if v[1]},
-                     "row_err_vs_f64_oracle": {"max": float(err.max()), "median": float(np.median(err)),
-                                               "rows": int(len(rows))}}
-        del dA
-        torch.cuda.empty_cache()
-    # the long rows' numeric pass by column buckets instead of merge rounds
-    # (option long_bucket; the same bits), FP64
-    dA = brm.to_device(A)
-
-    def bucket_step():
-        Cx = brm.brm_spgemm_precise(dA, dA, long_bucket=True)
-        del Cx
-
-    brm.brm_trace_reset()
-    brm.brm_trace_enable(True)
-    ms = _timed(bucket_step, args.steps, max(1, min(args.warmup, 2)))
-    t = brm.brm_trace_read()
-    brm.brm_trace_enable(False)
-    n_calls = args.steps + max(1, min(args.warmup, 2))
-    out["f64_long_bucket"] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9,
-                              "phases_ms": {k: round(v[0] / n_calls, 3) for k, v in t.items() if v[1]}}
-    del dA
-    torch.cuda.empty_cache()
-    # BRMerge-Upper: C_bar of every product (about 251 GB here) does not fit
-    # beside C, so it runs in row chunks
-    dA = brm.to_device(A)
-    try:
-        def upper_step():
-            Cx = brm.brm_spgemm_upper(dA, dA, upper_chunk_bytes=16 << 30)
-            del Cx
-
-        ms = _timed(upper_step, 1, 1)
-        out["f64_upper_chunked"] = {"ms_per_step": ms, "gflops": 2.0 * total / (ms * 1e-3) / 1e9,
-                                    "chunk_bytes": 16 << 30}
-    except brm.BrmError as e:
-        out["f64_upper_chunked"] = {"error": str(e)}
-    del dA
-    torch.cuda.empty_cache()
-    out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
-    out["speedup_f32_twosum_vs_f64"] = out["f64"]["ms_per_step"] / out["f32_twosum"]["ms_per_step"]
-    print(json.dumps(out), flush=True)
-
-
-def run_batched(args):
-    """512 uneven products: one batched call vs 512 single calls, the numeric
-    pass replayed from a CUDA graph, autotuned bins; FP64 and FP32."""
-    import torch
-    import oracle
-    from paper_2206_06611_gb300 import brm
-    torch.cuda.set_device(0)
-    out = {"workload": "batched: 512 products A_i*A_i, n_i log-uniform in [1e3, 2e5], half 3-D Laplacian, "
-                       "half ER with 4..32 per row"}
-    mats64 = I.batched_mix(512)
-    total = int(sum(oracle.row_nprod(M, M).sum() for M in mats64))
-    for name, dtype in (("f64", np.float64), ("f32", np.float32)):
-        mats = [M.astype(dtype) for M in mats64]
-        dev = [brm.to_device(M) for M in mats]
-        gf = lambda ms: 2.0 * total / (ms * 1e-3) / 1e9  # noqa: E731
-
-        def batched():
-            C, _ = brm.brm_spgemm_batched(dev, dev)
-            del C
-
-        def separate():
-            for d in dev:
-                C = brm.brm_spgemm_precise(d, d)
-                del C
-
-        r = {"nprod": total, "rows": int(sum(M.rows for M in mats))}
-        r["separate_ms"] = _timed(separate, max(1, args.steps // 2), 1)
-        r["batched_ms"] = _timed(batched, args.steps, 2)
-        opts, tune_ms = brm.brm_autotune(dev, dev)
-        r["autotuned"] = {"reg_keys": opts["reg_keys"], "reg_warps": opts["reg_warps"], "tune_call_ms": tune_ms}
-
-        def batched_tuned():
-            C, _ = brm.brm_spgemm_batched(dev, dev, **opts)
-            del C
-
-        r["batched_tuned_ms"] = _timed(batched_tuned, args.steps, 2)
-        b = brm.Batch(dev, dev, **opts)
-        r["numeric_graph_ms"] = _timed(b.graph_launch, args.steps, 2)
-        r["numeric_launch_ms"] = _timed(b.numeric, args.steps, 2)
-        b.check()
-        b.close()
-        for k in ("separate_ms", "batched_ms", "batched_tuned_ms"):
-            r[k.replace("_ms", "_gflops")] = gf(r[k])
-        r["speedup_batched_vs_separate"] = r["separate_ms"] / r["batched_tuned_ms"]
-        out[name] = r
-        del dev
-        torch.cuda.empty_cache()
-    print(json.dumps(out), flush=True)
-
-
-def run_diff(args):
-    """Differentiable C = A*B (A R-MAT scale 18 ef16, B ER 2^18 with 8 per row,
-    FP32 N(0,1)): forward + hand-written backward, and the FP64 plain forward."""
-    import torch
-    import oracle
-    from paper_2206_06611_gb300 import brm
-    torch.cuda.set_device(0)
-    A = I.normal_values(I.rmat(18, 16), 101)
-    B = I.normal_values(I.erdos_renyi(1 << 18, 8), 102)
-    total = int(oracle.row_nprod(A, B).sum())
-    dA, dB = brm.to_device(A), brm.to_device(B)
-    a_val = dA.val.clone().requires_grad_(True)
-    b_val = dB.val.clone().requires_grad_(True)
-    Aq = brm.DeviceCSR(A.rows, A.cols, dA.rp, dA.col, a_val)
-    Bq = brm.DeviceCSR(B.rows, B.cols, dB.rp, dB.col, b_val)
-    C = brm.spgemm(Aq, Bq)
-    G = torch.from_numpy(I.rand_normal(103, I.S_GRAD, np.arange(C.nnz)).astype(np.float32)).cuda()
-    del C
-
-    def fwd():
-        Cx = brm.spgemm(Aq, Bq)
-        del Cx
-
-    def fwd_bwd():
-        Cx = brm.spgemm(Aq, Bq)
-        (Cx.val * G).sum().backward()
-        a_val.grad = None
-        b_val.grad = None
-
-    C = brm.spgemm(Aq, Bq)
-    Cd = brm.DeviceCSR(C.rows, C.cols, C.rp, C.col, None)
-    del C
-
-    def bwd_only():
-        brm.brm_spgemm_backward(dA, dB, Cd, G)
-
-    d64A, d64B = brm.to_device(A.astype(np.float64)), brm.to_device(B.astype(np.float64))
-
-    def fwd64():
-        Cx = brm.brm_spgemm_precise(d64A, d64B)
-        del Cx
-
-    out = {"workload": "differentiable C=A*B, A R-MAT scale 18 ef16, B ER 2^18 8/row, FP32 N(0,1)",
-           "nprod": total}
-    out["fwd_f32_ms"] = _timed(fwd, args.steps, 3)
-    out["bwd_f32_ms"] = _timed(bwd_only, args.steps, 3)
-    out["fwd_bwd_f32_ms"] = _timed(fwd_bwd, args.steps, 3)
-    out["fwd_f64_plain_ms"] = _timed(fwd64, args.steps, 3)
-    out["speedup_f32_fwd_vs_f64_plain"] = out["fwd_f64_plain_ms"] / out["fwd_f32_ms"]
-    out["fwd_f32_gflops"] = 2.0 * total / (out["fwd_f32_ms"] * 1e-3) / 1e9
-    print(json.dumps(out), flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -611,11 +713,13 @@ def main():
     ap.add_argument("--impl", default="brm", choices=["brm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--headline-only", action="store_true", help="skip the 'also' block")
     ap.add_argument("--profile", action="store_true", help="two calls only (for ncu captures)")
     ap.add_argument("--profile-n", type=int, default=1 << 20)
-    ap.add_argument("--workload", default="er", choices=["er", "rmat", "batched", "diff"],
-                    help="er: the headline line; the others print their own JSON line")
-    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of --workload rmat")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "batched", "diff"],
+                    help="rmat (default) or er: the headline line; batched / diff: --profile only")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="--profile --workload batched: products of the mix (the first of the 512)")
     ap.add_argument("--long-bucket", action="store_true",
@@ -623,14 +727,10 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
-    elif args.workload == "rmat":
-        run_rmat(args)
-    elif args.workload == "batched":
-        run_batched(args)
-    elif args.workload == "diff":
-        run_diff(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("batched", "diff"):
+        raise SystemExit("--workload batched/diff only with --profile (their numbers are in the 'also' block)")
     else:
         run_gpu(args)
 

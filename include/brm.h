@@ -359,7 +359,7 @@ void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);
 
 /*
  * Per-row statistics used by the binning (step 1 of both libraries, Section
- * III-D; Algorithm 1 line 1): nprod_i = sum over k in A_i* of |B_k*|.
+ * III-D; the buffer sizing that opens Algorithm 1): nprod_i = sum over k in A_i* of |B_k*|.
  *   row_nprod   device int64[A.rows], caller-allocated.
  *   total_nprod, max_row_nprod, max_row_nnz_A: host int64*, may be NULL.
  * Synchronises the stream once.

@@ -21,9 +21,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // ---------------------------------------------------------------------------
-// Step 1 of both libraries (Section III-D; Algorithm 1 line 1): per row the
-// intermediate-product count nprod_i = sum over k in A_i* of |B_k*| and the
-// list count L_i = |A_i*|.  The paper then splits rows statically into p
+// Step 1 of both libraries (Section III-D; the buffer sizing that opens
+// Algorithm 1): per row the intermediate-product count
+// nprod_i = sum over k in A_i* of |B_k*| and the list count L_i = |A_i*|.  The paper then splits rows statically into p
 // groups of equal nprod for p CPU threads (Section III-D); on the GPU rows are
 // instead sorted into bins by size, each bin served by a kernel whose thread
 // group and buffer location fit that size.  This pass classifies the rows and

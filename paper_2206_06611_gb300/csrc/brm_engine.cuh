@@ -870,7 +870,7 @@ __device__ __forceinline__ int round_of(const G &g, int nl, const Buf<P> s, cons
 // Whole row (Algorithm 1 for one i): the multiplying phase into b0, merging
 // rounds between b0 and b1 while more than two lists are left, then the last
 // round -- or, for a row of one list, a copy -- into the row's output slot
-// (the last line of Algorithm 1).  Numeric passes write C (or C_bar) at
+// (the store that ends Algorithm 1).  Numeric passes write C (or C_bar) at
 // out_rp[row]; every pass may record the row length in out_cnt[row].
 template <class P, class G, int K, int UNR, bool kTiled = false>
 __device__ __forceinline__ void brm_row(const G &g, int row, const RowJob &j, const Buf<P> &b0, const Buf<P> &b1,

@@ -110,3 +110,38 @@ def bins_matrix(seed=3):
     acol = np.concatenate(rows_a).astype(np.int32)
     A = I.CSR(len(rows_a), k, arp.astype(np.int32), acol, I.rand_sym(seed, 25, np.arange(len(acol))))
     return A, B
+
+
+def device_rows(C, rows):
+    """(row_ptr, col, val as float64) of the given rows of a device result,
+    gathered on the device (for results too large to copy to the host)."""
+    import torch
+    rows = np.asarray(rows, dtype=np.int64)
+    rp = C.rp.cpu().numpy()
+    starts, ends = rp[rows], rp[rows + 1]
+    idx = np.concatenate([np.arange(a, b, dtype=np.int64) for a, b in zip(starts, ends)]) if len(rows) else \
+        np.zeros(0, np.int64)
+    it = torch.from_numpy(idx).to(C.col.device)
+    crp = np.zeros(len(rows) + 1, dtype=np.int64)
+    crp[1:] = np.cumsum(ends - starts)
+    return crp, C.col[it].cpu().numpy(), C.val[it].cpu().numpy().astype(np.float64)
+
+
+def assert_sample_exact(crp, col, val, ref):
+    """Sampled rows (crp, col, val) equal to an oracle Result of the same rows."""
+    assert np.array_equal(crp, ref.crp), "row lengths differ"
+    assert np.array_equal(col, ref.col), "column indices differ"
+    bad = np.nonzero(~(val == ref.val))[0]
+    assert len(bad) == 0, f"{len(bad)} values differ, first at {bad[:5]}: {val[bad[:5]]} vs {ref.val[bad[:5]]}"
+
+
+def straddling_rows(rp, marks):
+    """Rows whose slice of C contains one of the offsets in `marks` (and the
+    rows right before and after them)."""
+    out = []
+    m = len(rp) - 1
+    for x in marks:
+        if x < rp[-1]:
+            i = int(np.searchsorted(rp, x, side="right")) - 1
+            out += [j for j in (i - 1, i, i + 1) if 0 <= j < m]
+    return np.array(sorted(set(out)), dtype=np.int64)
