@@ -158,6 +158,15 @@ typedef struct {
  *                  32 GiB, per chunk).  A smaller budget runs fewer
  *                  persistent blocks (merge rounds) or more batches (column
  *                  buckets).
+ *   long_window    1: rows beyond block_max_nprod are cut into column
+ *                  windows of at most 1024 products (the symbolic pass plans
+ *                  them from a column bitmap and a product histogram), spread
+ *                  over many warps, each window's keys sorted in registers by
+ *                  one warp and every column summed in the merge tree's order
+ *                  (the same values as the merge rounds), when long_bucket is
+ *                  0, B has at most 2^24 columns and every such row at most
+ *                  65535 lists (BRMerge-Upper in row chunks keeps the merge
+ *                  rounds); 0 (default): the arena merge rounds.
  *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
  *                  sizeof value) bytes) processed at once; a larger product
  *                  is processed in row chunks of at most this size, each
@@ -181,6 +190,7 @@ typedef struct {
     int32_t long_bucket;
     size_t arena_bytes;
     size_t upper_chunk_bytes;
+    int32_t long_window;
 } brm_options;
 
 void brm_options_default(brm_options *opts);

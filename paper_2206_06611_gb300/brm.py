@@ -56,7 +56,8 @@ class brm_options(ctypes.Structure):
                 ("reg_num_half", ctypes.c_int32), ("reg_num_direct", ctypes.c_int32),
                 ("long_bucket", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_size_t),
-                ("upper_chunk_bytes", ctypes.c_size_t)]
+                ("upper_chunk_bytes", ctypes.c_size_t),
+                ("long_window", ctypes.c_int32)]
 
 
 class BrmError(RuntimeError):
@@ -247,7 +248,8 @@ def _stream(stream=None):
 
 def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
             reg_keys=0, reg_warps=0, symbolic_hash=False, reg_top=True, reg_perm=True, reg_num_half=True,
-            reg_num_direct=True, long_bucket=False, arena_bytes=0, upper_chunk_bytes=0) -> brm_options:
+            reg_num_direct=True, long_bucket=False, arena_bytes=0, upper_chunk_bytes=0,
+            long_window=False) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -270,6 +272,7 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
     o.long_bucket = int(bool(long_bucket))
     o.arena_bytes = arena_bytes
     o.upper_chunk_bytes = upper_chunk_bytes
+    o.long_window = int(bool(long_window))
     return o
 
 

@@ -248,6 +248,7 @@ brm_options resolve(const brm_options *o) {
     r.reg_num_half = r.reg_num_half != 0 ? 1 : 0;
     r.reg_num_direct = r.reg_num_direct != 0 ? 1 : 0;
     r.long_bucket = r.long_bucket != 0 ? 1 : 0;
+    r.long_window = r.long_window != 0 ? 1 : 0;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -415,11 +416,80 @@ struct LongPlan {
     int32_t *ctr = nullptr;
 };
 
+// Long rows by column windows (brm_long_win.cuh): the plan's arrays, kept
+// from the pass that computes them (the symbolic pass of BRMerge-Precise and
+// of prepared batches; the numeric pass itself in BRMerge-Upper) to the
+// numeric pass, and the numeric kernel's per-warp scratch.
+struct WinPlan {
+    bool on = false;
+    bool planned = false;          // a pass has launched the plan kernel
+    WinRec *rec = nullptr;
+    int64_t *base = nullptr;
+    int32_t *n = nullptr, *nws = nullptr;
+    int64_t *rownnz = nullptr;
+    int2 *spans = nullptr;
+    unsigned long long *ctr = nullptr;
+    int4 *cur = nullptr;
+    void *hot = nullptr;
+    int32_t maxL = 0, grid = 0;
+};
+
+// Whether the long rows of these passes take the column windows, and their
+// arrays: when the option is on, the bucket option off, B has at most 2^24
+// columns and every long row at most kWinMaxL lists.
+int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKind vnum, WinPlan &wp) {
+    wp = WinPlan{};
+    const int64_t nl = (int64_t)pl.long_rows_h.size();
+    if (nl == 0 || !o.long_window || o.long_bucket || bcols > kLbMaxCols) return BRM_OK;
+    int64_t maxL = 0;
+    for (int64_t s = 0; s < nl; ++s) maxL = std::max<int64_t>(maxL, pl.long_L_h[s]);
+    if (maxL > kWinMaxL) return BRM_OK;
+    std::vector<int64_t> base((size_t)nl + 1, 0);
+    int64_t spans = 0;
+    for (int64_t s = 0; s < nl; ++s) {
+        base[s + 1] = base[s] + win_cap(pl.long_nprod_h[s], bcols);
+        spans += win_span_cap(pl.long_nprod_h[s]);
+    }
+    wp.maxL = (int32_t)std::max<int64_t>(maxL, 1);
+    wp.grid = long_win_grid(vnum == kIdx ? kF64 : vnum);
+    const size_t warps = (size_t)wp.grid * kWinWarps;
+    int rc;
+    if ((rc = get(mem, wp.base, (size_t)nl + 1, "window offsets"))) return rc;
+    if ((rc = get(mem, wp.rec, (size_t)std::max<int64_t>(base[nl], 1), "windows"))) return rc;
+    if ((rc = get(mem, wp.n, (size_t)nl, "window counts"))) return rc;
+    if ((rc = get(mem, wp.nws, (size_t)nl, "windows per span"))) return rc;
+    if ((rc = get(mem, wp.rownnz, (size_t)nl, "long-row lengths"))) return rc;
+    if ((rc = get(mem, wp.spans, (size_t)std::max<int64_t>(spans, 1), "window spans"))) return rc;
+    if ((rc = get(mem, wp.ctr, 2, "span counters"))) return rc;
+    if ((rc = get(mem, wp.cur, warps * (size_t)wp.maxL, "list cursors"))) return rc;
+    if (!(wp.hot = mem.get(warps * kWinHotBytes))) return fail(BRM_ERR_OOM, "hot-window scratch");
+    BRM_CUDA(cudaMemcpyAsync(wp.base, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
+    BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
+    wp.on = true;
+    return BRM_OK;
+}
+
+// The window fields of a long-row job.
+void win_job(RowJob &jb, const WinPlan &wp, bool plan_here) {
+    jb.win = wp.rec;
+    jb.win_base = wp.base;
+    jb.win_n = wp.n;
+    jb.win_nws = wp.nws;
+    jb.win_rownnz = wp.rownnz;
+    jb.win_spans = wp.spans;
+    jb.win_ctr = wp.ctr;
+    jb.win_cur = wp.cur;
+    jb.win_hot = wp.hot;
+    jb.win_maxL = wp.maxL;
+    jb.win_grid = wp.grid;
+    jb.win_plan = plan_here ? 1 : 0;
+}
+
 int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp,
-              bool persistent = true) {
+              bool persistent = true, const WinPlan *wp = nullptr) {
     const int64_t nl = (int64_t)pl.long_rows_h.size();
     lp.starts.clear();
-    if (nl == 0) return BRM_OK;
+    if (nl == 0 || (wp && wp->on)) return BRM_OK;
     // the symbolic pass counts long rows with the column bitmap whenever B has
     // at most 2^24 columns; the numeric pass uses column buckets on request
     // (they pack a list index into 16 bits and cut B's columns into at most
@@ -517,7 +587,8 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
 
 // Kernel launches of one pass over every bin (no host synchronisation, no
 // allocation: a numeric pass of a prepared plan can be captured in a graph).
-int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cudaStream_t st, bool trace) {
+int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cudaStream_t st, bool trace,
+                const WinPlan *wp = nullptr) {
     for (int b = kBinReg0; b <= kBinBlock; ++b) {
         RowJob jb = j;
         jb.rows = pl.rows + pl.base[b];
@@ -526,6 +597,17 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         const int ph = b < kBinWarp ? kPhSymReg : kPhSymWarp + (b - kBinWarp);
         PhaseScope ps(trace ? (v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg)) : -1, st);
         BRM_CUDA(launch_rows(v, b, jb, st));
+    }
+    if (wp && wp->on) {
+        // every long row in one launch (two with the plan)
+        RowJob jb = j;
+        jb.rows = pl.long_rows_s;
+        jb.count = (int32_t)pl.long_rows_h.size();
+        jb.slot_nprod = pl.long_nprod_s;
+        win_job(jb, *wp, v == kIdx || !wp->planned);
+        PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
+        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
+        return BRM_OK;
     }
     if (lp.starts.size() < 2) return BRM_OK;
     PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
@@ -556,11 +638,13 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
 }
 
 // One BRMerge pass (symbolic or numeric) over all bins.
-int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j, bool persistent = true) {
+int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j, bool persistent = true,
+             WinPlan *wp = nullptr) {
     LongPlan lp;
-    int rc = plan_long(mem, v, pl, o, j.bcols, lp, persistent);
+    int rc = plan_long(mem, v, pl, o, j.bcols, lp, persistent, wp);
     if (rc) return rc;
-    if ((rc = launch_pass(v, pl, lp, j, mem.st, true))) return rc;
+    if ((rc = launch_pass(v, pl, lp, j, mem.st, true, wp))) return rc;
+    if (wp && wp->on) wp->planned = true;
     if (lp.arena) {
         mem.free_one(lp.arena);   // stream-ordered release after the launches
         mem.free_one(lp.off_d);
@@ -614,12 +698,13 @@ struct PermBuf {
 };
 
 int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *row_ptr, int64_t *nnz,
-                  PermBuf *pb = nullptr) {
+                  PermBuf *pb = nullptr, WinPlan *wp = nullptr) {
     const int64_t m = src.m;
     int64_t *row_nnz;
     int rc = get(mem, row_nnz, (size_t)std::max<int64_t>(m, 1), "row counts");
     if (rc) return rc;
     if ((rc = make_plan(mem, src, o, pl, nullptr, row_nnz))) return rc;
+    if (wp && (rc = plan_win(mem, pl, o, src.bcols, value_kind(src.dtype, o), *wp))) return rc;
     void *tmp;
     if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
     RowJob j = base_job(src, o);
@@ -641,7 +726,7 @@ int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int6
         j.perm = pb->perm;
         j.perm_off = pb->perm_off;
     }
-    if ((rc = run_pass(mem, kIdx, pl, o, j))) return rc;
+    if ((rc = run_pass(mem, kIdx, pl, o, j, true, wp))) return rc;
     {
         PhaseScope ps(kPhScan, mem.st);
         BRM_CUDA(launch_scan(row_nnz, row_ptr, m, tmp, mem.st));
@@ -670,7 +755,8 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     int64_t nnz = 0;
     const Src src = src_of(A, B);
     PermBuf pb;
-    if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz, &pb))) return rc;
+    WinPlan wp;
+    if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz, &pb, &wp))) return rc;
     int32_t *col;
     if ((rc = get_own(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
     void *val = mem.get_direct((size_t)std::max<int64_t>(nnz, 1) * value_bytes(A->dtype));
@@ -686,7 +772,7 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
     j.exact = 1;
-    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
+    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j, true, &wp))) return rc;
     if ((rc = check_flag(mem, err))) return rc;
     mem.detach(rp);
     mem.detach(col);
@@ -876,7 +962,9 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
-    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j))) return rc;
+    WinPlan wp;
+    if ((rc = plan_win(mem, pl, o, src.bcols, value_kind(A->dtype, o), wp))) return rc;
+    if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j, true, &wp))) return rc;
     // step 5: prefix sum of the row sizes, allocation of C
     if ((rc = get_own(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
     {
@@ -980,6 +1068,7 @@ struct brm_batch {
     brm::LongPlan lp;
     brm::RowJob job{};
     brm::PermBuf pb;
+    brm::WinPlan wp;
     brm::VKind v = brm::kF64;
     int32_t count = 0;
     int64_t nnz = 0;
@@ -1020,7 +1109,7 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     const int64_t M = b->src.m;
     if (!rc) rc = get_own(b->mem, b->rp, (size_t)M + 1, "C.row_ptr");
     if (!rc) b->mem.reserve(row_workspace_bytes(M));
-    if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz, &b->pb);
+    if (!rc) rc = symbolic_into(b->mem, b->src, b->o, b->pl, b->rp, &b->nnz, &b->pb, &b->wp);
     if (!rc) rc = get_own(b->mem, b->col, (size_t)std::max<int64_t>(b->nnz, 1), "C.col_idx");
     if (!rc) {
         b->val = b->mem.get_direct((size_t)std::max<int64_t>(b->nnz, 1) * value_bytes(b->src.dtype));
@@ -1028,7 +1117,7 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     }
     if (!rc) rc = get(b->mem, b->err, 1, "error flag");
     b->v = value_kind(b->src.dtype, b->o);
-    if (!rc) rc = plan_long(b->mem, b->v, b->pl, b->o, b->src.bcols, b->lp);
+    if (!rc) rc = plan_long(b->mem, b->v, b->pl, b->o, b->src.bcols, b->lp, true, &b->wp);
     if (rc) {
         delete b;
         return rc;
@@ -1049,7 +1138,7 @@ int batch_create(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
 // The numeric pass of a prepared batch: launches only.
 int batch_numeric(brm_batch *b, cudaStream_t st, bool trace) {
     BRM_CUDA(cudaMemsetAsync(b->err, 0, sizeof(unsigned int), st));
-    return launch_pass(b->v, b->pl, b->lp, b->job, st, trace);
+    return launch_pass(b->v, b->pl, b->lp, b->job, st, trace, &b->wp);
 }
 
 int batch_check(brm_batch *b, cudaStream_t st) {
@@ -1128,6 +1217,7 @@ void brm_options_default(brm_options *o) {
     o->long_bucket = 0;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
+    o->long_window = 0;
 }
 
 const char *brm_last_error(void) { return g_err.c_str(); }

@@ -385,6 +385,9 @@ extern size_t long_bytes_f64(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_f32(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_f32c(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_idx(int64_t n, int64_t L, bool bucket);
+extern int win_grid_f64();
+extern int win_grid_f32();
+extern int win_grid_f32c();
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st) {
     switch (v) {
@@ -401,6 +404,15 @@ size_t long_row_bytes_for(VKind v, int64_t n, int64_t L, bool bucket) {
         case kF32: return long_bytes_f32(n, L, bucket);
         case kF32C: return long_bytes_f32c(n, L, bucket);
         default: return long_bytes_idx(n, L, bucket);
+    }
+}
+
+int long_win_grid(VKind v) {
+    switch (v) {
+        case kF64: return win_grid_f64();
+        case kF32: return win_grid_f32();
+        case kF32C: return win_grid_f32c();
+        default: return 0;
     }
 }
 

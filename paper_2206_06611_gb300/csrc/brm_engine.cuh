@@ -218,6 +218,23 @@ struct RowJob {
     // from the counter (zero at launch), in the arena at arena_off[b]
     int32_t *long_ctr;
     int32_t long_grid;
+    // long rows by column windows (brm_long_win.cuh): per long slot, where its
+    // windows start (count + 1 entries), how many it has, windows per span,
+    // the row's distinct columns; the span list and its two counters (spans
+    // written, spans taken); per warp of the numeric kernel a cursor per list
+    // (win_maxL of them) and the state of a hot window
+    struct WinRec *win;
+    const int64_t *win_base;
+    int32_t *win_n;
+    int32_t *win_nws;
+    int64_t *win_rownnz;
+    int2 *win_spans;
+    unsigned long long *win_ctr;
+    int4 *win_cur;
+    void *win_hot;
+    int32_t win_maxL;
+    int32_t win_grid;       // blocks of the numeric kernel (its scratch is sized for them)
+    int32_t win_plan;       // 1: this pass computes the plan first (symbolic pass, or Upper)
 };
 
 // The inputs one output row needs: its row of A (columns and values from the

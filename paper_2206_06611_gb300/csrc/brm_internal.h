@@ -63,6 +63,52 @@ constexpr int kLbSlots = 65536;
 constexpr int kLbHotPerSm = 2;
 __host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUnit + 1) + 1; }
 
+// Long rows by column windows (brm_long_win.cuh): a window holds fewer than
+// kWinP products (one warp sorts them: 32 lanes x 32 keys) unless it is a
+// single cell of at most kWinCellMax columns; cuts every kWinH products;
+// at most kWinCells cells per bitmap window of kWinBitmapCols columns; rows
+// of at most kWinMaxL lists; spans of at least max(kWinSpanMin,
+// kWinSpanPerList * L) products; kWinWarps warps per block.
+constexpr int kWinP = 1024;
+constexpr int kWinH = kWinP / 2;
+constexpr int kWinPBits = 10;
+constexpr int64_t kWinBitmapCols = (int64_t)1 << 20;
+constexpr int kWinCells = 8192;
+constexpr int kWinCellMax = (int)(kWinBitmapCols / kWinCells);
+constexpr int kWinMaxL = 65535;
+constexpr int64_t kWinSpanMin = 32768;
+constexpr int kWinSpanPerList = 16;
+constexpr int kWinWarps = 4;
+// per-warp scratch of the window kernel: for kWinCellMax columns an 8-byte
+// top sum, a level mask, the last list and 16 pending 8-byte sums; 16 closed
+// 8-byte sums per lane; rounded to 256
+constexpr size_t kWinHotBytes = ((size_t)((8 + 4 + 4 + 8 * 16) * kWinCellMax + 8 * 16 * 32) + 255) / 256 * 256;
+static_assert(kWinP == 32 * 32 && (1 << kWinPBits) == kWinP, "a window is sorted by one warp, 32 keys per lane");
+static_assert(kWinCellMax == 128, "cells are at most 128 columns wide");
+static_assert((kWinBitmapCols << kWinPBits) <= ((int64_t)1 << 32) - 1, "key = column offset and position");
+
+// One window of a long row: first column, products, and the number of the
+// row's distinct columns before it (its output offset inside the row).
+struct WinRec {
+    int32_t c0;
+    int32_t np;
+    int64_t off;
+};
+static_assert(sizeof(WinRec) == 16, "window record size");
+
+// Windows a row of n products can produce over B's columns (ncols): every
+// bitmap window holds at most 3 n_w / kWinH + 1 cuts, and never more than its
+// cells.
+__host__ __device__ constexpr int64_t win_cap(int64_t n, int64_t ncols) {
+    const int64_t nbw = ncols > 0 ? (ncols + kWinBitmapCols - 1) / kWinBitmapCols : 1;
+    const int64_t a = 3 * ((n + kWinH - 1) / kWinH) + nbw;
+    const int64_t b = nbw * kWinCells;
+    return a < b ? a : b;
+}
+
+// Spans a row of n products can produce: at most 2 n / kWinSpanMin + 2.
+__host__ __device__ constexpr int64_t win_span_cap(int64_t n) { return 2 * (n / kWinSpanMin) + 2; }
+
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {
     kPhValidate = 0, kPhBin, kPhSymReg, kPhSymWarp, kPhSymBlock, kPhSymLong, kPhScan,
@@ -77,6 +123,8 @@ enum VKind { kIdx = 0, kF64 = 1, kF32 = 2, kF32C = 3 };
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st);
 size_t long_row_bytes_for(VKind v, int64_t nprod, int64_t L, bool bucket);
+// blocks of the long-row window kernel of a value kind (0 for kIdx)
+int long_win_grid(VKind v);
 
 // Statistics written by the binning kernels.
 struct BinStats {

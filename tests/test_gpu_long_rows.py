@@ -187,9 +187,9 @@ def test_arena_rounds_many_tiles_and_empty_pairs(mode, dtype, comp):
     B = csr_from_rows(rows, ncols, 104, 1)
     A = csr_from_rows([np.arange(3000), np.arange(3000, k), np.array([5, 3000, 4000, 59000])], k, 105, 2)
     ref = oracle.alg1(A, B, prec=mode)
-    C = run(A, B, "precise", dtype, comp, long_bucket=False)
+    C = run(A, B, "precise", dtype, comp, long_bucket=False, long_window=False)
     assert_rows_exact(C, ref)
-    same(C, run(A, B, "upper", dtype, comp, long_bucket=False))
+    same(C, run(A, B, "upper", dtype, comp, long_bucket=False, long_window=False))
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
@@ -199,9 +199,9 @@ def test_persistent_blocks_share_arena_slots(mode, dtype, comp):
     byte a single block merges them all.  Same bits as the default run and as
     the oracle on the largest rows."""
     R = I.rmat(14, 16, seed=83)
-    C = run(R, R, "precise", dtype, comp, long_bucket=False)
-    same(C, run(R, R, "precise", dtype, comp, long_bucket=False, arena_bytes=1))
-    same(C, run(R, R, "upper", dtype, comp, long_bucket=False, arena_bytes=1 << 20))
+    C = run(R, R, "precise", dtype, comp, long_bucket=False, long_window=False)
+    same(C, run(R, R, "precise", dtype, comp, long_bucket=False, long_window=False, arena_bytes=1))
+    same(C, run(R, R, "upper", dtype, comp, long_bucket=False, long_window=False, arena_bytes=1 << 20))
     nprod = oracle.row_nprod(R, R)
     rows = np.sort(np.argsort(-nprod, kind="stable")[:40])
     assert_rows_exact(C, oracle.alg1(R, R, rows, prec=mode), rows)

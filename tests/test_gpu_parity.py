@@ -156,10 +156,12 @@ def test_upper_in_row_chunks(chunk):
 
 def test_long_rows_small_arena_batches():
     """A tiny arena budget: one persistent block merges every long row, one
-    after another, in one arena slot."""
+    after another, in one arena slot (merge rounds; the column windows need
+    no arena)."""
     A, B = bins_matrix(seed=5)
     ref = oracle.alg1(A, B)
-    assert_rows_exact(run(A, B, arena_bytes=1), ref)
+    assert_rows_exact(run(A, B, arena_bytes=1, long_window=False), ref)
+    assert_rows_exact(run(A, B, arena_bytes=1, long_window=True), ref)
 
 
 # --------------------------------------------------------------------------
