@@ -256,9 +256,10 @@ int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
  * brm_spgemm_precise gives.
  *   A, B        inputs as for brm_spgemm_precise (values required).
  *   C_row_ptr   device int64[A.rows + 1], read only; must be the exact row
- *               pointer of A * B (a row whose merged length differs from its
- *               slot makes the call fail with BRM_ERR_INVALID, and nothing is
- *               written outside the slots).
+ *               pointer of A * B (a row whose length -- zero for a row
+ *               without products -- differs from its slot makes the call fail
+ *               with BRM_ERR_INVALID, and nothing is written outside the
+ *               slots).
  *   C_col_idx   device int32[nnz(C)], written.
  *   C_val       device float/double[nnz(C)] (A's dtype), written.
  *   opts        validate, compensated, warp_max_nprod and block_max_nprod as
@@ -269,8 +270,10 @@ int brm_spgemm_upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C,
  * Workspace: a fixed 5 MiB device array inside the library (held on every
  * GPU that loads it until the process exits) instead of allocations.  The
  * first call on a device looks up that array's address (cudaGetSymbolAddress)
- * with the device current, so make the first call on each device before any
- * stream capture starts.  Every call reuses the same array and clears the
+ * with the device current and keeps it for the life of the process, so make
+ * the first call on each device before any stream capture starts, and do not
+ * call this entry point again after cudaDeviceReset (the kept address would
+ * belong to the destroyed context).  Every call reuses the same array and clears the
  * parts that must start at zero; calls that overlap on the GPU (on different
  * streams or from different host threads) race on it and must be avoided.
  * Synchronises the stream twice (bins; the row-length check), three times
@@ -293,11 +296,14 @@ int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t
  *   dC           device values of G on C's pattern (A's dtype).
  *   dA_val       device, A.nnz values, written (NULL: not computed).
  *   dB_val       device, B.nnz values, overwritten (NULL: not computed).
- * One GPU thread per stored entry of A.  dA is summed sequentially per entry
- * (deterministic); dB is accumulated with atomic additions, so its rounding
- * may differ between runs.  Returns
- * BRM_ERR_INVALID if C's pattern misses a column.  Synchronises the stream
- * once.  opts is unused (may be NULL); alloc provides one 4-byte flag.
+ * Both are deterministic sums in a fixed order, each product rounded before
+ * it is added: dA_ik over B_k* in column order (one GPU thread per entry of
+ * A), dB_kj over the rows i in increasing order (one thread per entry of B,
+ * after A's entries are bucketed by column and every bucket is sorted).
+ * Returns BRM_ERR_INVALID if C's pattern misses a column.  Synchronises the
+ * stream once.  opts is unused (may be NULL); alloc provides a 4-byte flag
+ * and, when dB is computed, about 16 * A.cols + 8 * A.nnz bytes of
+ * workspace.
  */
 int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, const int32_t *C_col_idx,
                         const void *dC, void *dA_val, void *dB_val, const brm_options *opts,

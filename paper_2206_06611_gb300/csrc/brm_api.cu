@@ -1270,11 +1270,24 @@ int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row
     unsigned int *err;
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
-    const size_t vb = value_bytes(A->dtype);
-    if (dB_val && B->nnz > 0) BRM_CUDA(cudaMemsetAsync(dB_val, 0, (size_t)B->nnz * vb, st));
     BackwardArgs a{};
     a.m = A->rows;
     a.nnz_a = A->nnz;
+    a.ka = A->cols;
+    a.kb = B->rows;
+    a.nnz_b = B->nnz;
+    if (dB_val && B->nnz > 0 && A->nnz > 0) {
+        // A^T's rows for the ordered dB sums
+        const size_t ka = (size_t)std::max<int64_t>(A->cols, 1);
+        if ((rc = get(mem, a.ws_cnt, ka, "backward column counts"))) return rc;
+        if ((rc = get(mem, a.ws_colptr, ka + 1, "backward column starts"))) return rc;
+        if (!(a.ws_scan = mem.get(scan_tmp_bytes(A->cols)))) return fail(BRM_ERR_OOM, "backward scan workspace");
+        if ((rc = get(mem, a.ws_ent, (size_t)A->nnz, "backward column entries"))) return rc;
+        if ((rc = get(mem, a.ws_row, (size_t)A->nnz, "backward entry rows"))) return rc;
+    } else if (dB_val && B->nnz > 0) {
+        BRM_CUDA(cudaMemsetAsync(dB_val, 0, (size_t)B->nnz * value_bytes(A->dtype), st));   // A has no entries
+        dB_val = nullptr;
+    }
     a.arp = A->row_ptr;
     a.acol = A->col_idx;
     a.aval = A->val;
@@ -1574,6 +1587,8 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     a.bin_of = bin_of;
     a.st = stats;
     a.rows = rows;
+    a.out_rp = C_row_ptr;
+    a.out_err = err;
     BRM_CUDA(launch_bin(a, st));
     BRM_CUDA(cudaMemcpyAsync(&h, stats, sizeof h, cudaMemcpyDeviceToHost, st));
     BRM_CUDA(cudaStreamSynchronize(st));
@@ -1605,7 +1620,7 @@ int numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr
     unsigned int flag = 0;
     BRM_CUDA(cudaMemcpyAsync(&flag, err, sizeof flag, cudaMemcpyDeviceToHost, st));
     BRM_CUDA(cudaStreamSynchronize(st));
-    if (flag) return fail(BRM_ERR_INVALID, "a numeric row length disagrees with C_row_ptr");
+    if (flag) return fail(BRM_ERR_INVALID, "a row's length disagrees with its slot in C_row_ptr");
     return BRM_OK;
 }
 

@@ -97,6 +97,8 @@ __global__ void k_bin(BinArgs a) {
         if (a.nprod) a.nprod[i] = np;
         if (a.bin_of) a.bin_of[i] = (uint8_t)bin;
         if (bin == kBinEmpty && a.row_cnt) a.row_cnt[i] = 0;
+        // a given output row pointer must leave an empty row an empty slot
+        if (bin == kBinEmpty && a.out_rp && a.out_rp[i + 1] != a.out_rp[i]) atomicOr(a.out_err, 1u);
     }
 #pragma unroll
     for (int b = 0; b < kNumBins; ++b) {

@@ -152,6 +152,8 @@ struct BinArgs {
     int64_t *nprod;        // optional, per row
     uint8_t *bin_of;       // optional, per row: its bin
     int64_t *row_cnt;      // optional: rows of the empty bin get 0
+    const int64_t *out_rp; // optional: C's row pointer; an empty row with a slot sets *out_err
+    unsigned int *out_err;
     BinStats *st;
     // scatter pass
     int64_t base[kNumBins];
@@ -181,11 +183,17 @@ cudaError_t launch_compact(int64_t m, const int64_t *cbar_off, const int64_t *rp
 // Backward pass of C = A * B (brm_backward.cu).
 struct BackwardArgs {
     int64_t m, nnz_a;
+    int64_t ka, kb, nnz_b;    // A's columns (= B's rows), B's rows, B's entries
     const int32_t *arp, *acol; const void *aval;
     const int32_t *brp, *bcol; const void *bval;
     const int64_t *crp; const int32_t *ccol; const void *dC;
     void *dA, *dB;            // either may be null
     unsigned int *err;        // set when C's pattern lacks a column of some B_k*
+    // dB workspace (backward_ws_bytes): bucket sizes / cursors (ka), bucket
+    // starts (ka + 1), the scan's temporary, entry indices and rows (nnz_a)
+    int64_t *ws_cnt, *ws_colptr;
+    void *ws_scan;
+    int32_t *ws_ent, *ws_row;
 };
 cudaError_t launch_backward(const BackwardArgs &a, bool f64, cudaStream_t st);
 

@@ -6,9 +6,9 @@ must not take an allocation's implicit synchronisation, or a plug-in that may
 only write the buffers it is given.  Its workspace is a fixed array inside
 libbrm, shared by every call, so these checks call it twice in a row on
 different products -- a result that leaked state from the previous call
-would show -- and compare each result with brm_spgemm_precise (the same
-kernels with allocated workspace) bit for bit, the parity tests' FP64
-criterion for results of the same merge tree.
+would show -- and compare each result bit for bit with the CPU oracle's
+BRMerge rounds (Algorithm 1 in the same precision) and with
+brm_spgemm_precise (the same kernels with allocated workspace).
 
 The file is named so that pytest collects it last.
 """
@@ -17,7 +17,10 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2206_06611_gb300 import inputs as I
+
+from helpers import assert_rows_exact
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,6 +32,8 @@ from paper_2206_06611_gb300 import brm  # noqa: E402
 
 
 def _noalloc_like_precise(A, B, dtype=np.float64, compensated=False):
+    prec = "f64" if dtype == np.float64 else ("f32c" if compensated else "f32")
+    ref = oracle.alg1(A, B, prec=prec)
     dA, dB = brm.to_device(A, dtype=dtype), brm.to_device(B, dtype=dtype)
     want = brm.brm_spgemm_precise(dA, dB, compensated=compensated)
     torch.cuda.synchronize()
@@ -41,6 +46,7 @@ def _noalloc_like_precise(A, B, dtype=np.float64, compensated=False):
     assert torch.equal(got.rp, want.rp)
     assert torch.equal(got.col, want.col)
     assert torch.equal(got.val, want.val)
+    assert_rows_exact(got, ref)
     return got
 
 
@@ -94,3 +100,27 @@ def test_noalloc_rejects_rows_beyond_its_limits():
         brm.brm_spgemm_numeric_noalloc(dA, dB, rp, col, val)
     assert e.value.code == -5
     assert bool((col == -7).all())
+
+
+def test_noalloc_rejects_a_slot_for_an_empty_row():
+    """A row pointer that gives a row without products a slot of one entry
+    (every later row shifted by one): the call fails with BRM_ERR_INVALID."""
+    A = I.erdos_renyi(300, 5, seed=27, ncols=200)
+    Z = I.CSR(5, 200, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    A = _stack([A, Z, I.erdos_renyi(40, 5, seed=28, ncols=200)])
+    B = I.erdos_renyi(200, 6, seed=29, ncols=700)
+    dA, dB = brm.to_device(A), brm.to_device(B)
+    rp, nnz = brm.brm_spgemm_symbolic(dA, dB)
+    empty_row = 302
+    assert int(rp[empty_row + 1] - rp[empty_row]) == 0
+    bad = rp.clone()
+    bad[empty_row + 1:] += 1
+    col = torch.zeros(nnz + 1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(nnz + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(brm.BrmError) as e:
+        brm.brm_spgemm_numeric_noalloc(dA, dB, bad, col, val)
+    assert e.value.code == -1
+    # the same arrays with the right row pointer: accepted, the oracle's result
+    got = brm.brm_spgemm_numeric_noalloc(dA, dB, rp, col[:nnz], val[:nnz])
+    torch.cuda.synchronize()
+    assert_rows_exact(got, oracle.alg1(A, B))
