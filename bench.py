@@ -55,9 +55,11 @@ BLOCK_MAX_L = 1024
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture of the current source of that kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, scaled to one full launch as the profile says), or
-# None when the kernel changed after the capture.
-TRAFFIC = {"numeric_long": None, "numeric_reg": None}
+# dram__bytes_write.sum), or None when the kernel changed after the capture:
+# numeric_long -- k_rows_long<PF64> captured at R-MAT scale 16 (39.14 GB) and
+# scaled by the long rows' products to scale 20 (x 55.89); numeric_reg --
+# k_rows_perm<PF64, 32, 8> on the ER workload itself.
+TRAFFIC = {"numeric_long": 39.144e9 * 20664164109 / 369754535, "numeric_reg": 3.900762e9 + 3.183467e9}
 
 
 def workload_name(scale: int) -> str:
@@ -451,7 +453,9 @@ def run_gpu(args):
         L = np.diff(A.rp.astype(np.int64))
         mask = (nprod > 0) & (nprod <= 1024) & (L <= 256)
     per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in trace.items() if v[1]}
-    roof = roofline(per_step, phase, numeric_bytes(A, A, mask, row_nnz, vbytes), phase)
+    # the traffic figures are for the workloads the captures scaled to
+    tkey = phase if (args.workload == "er" or args.scale == 20) else None
+    roof = roofline(per_step, phase, numeric_bytes(A, A, mask, row_nnz, vbytes), tkey)
     phases = {k: round(v[0], 4) for k, v in per_step.items()}
 
     # ---- CPU oracle on bounded samples ---------------------------------------
@@ -487,6 +491,7 @@ def run_gpu(args):
         if args.workload != "er":
             also["er"] = _guard(extra_er, args)
             also["rmat_precision"] = _guard(extra_rmat_precision, args, A, nprod, ms_max / args.steps)
+            also["rmat_symbolic"] = _guard(extra_symbolic, args, A)
         also["batched"] = _guard(extra_batched, args)
         also["differentiable"] = _guard(extra_diff, args)
         line["also"] = also
@@ -559,6 +564,18 @@ def extra_rmat_precision(args, A, nprod, ms_f64):
                      "phases_ms": {k: round(v[0], 3) for k, v in tr.items()}}
         del dA
         torch.cuda.empty_cache()
+    return out
+
+
+def extra_symbolic(args, A):
+    """The symbolic pass of the same R-MAT product by sorting (default) and by
+    the paper's hashing (option symbolic_hash): per-phase device times."""
+    from paper_2206_06611_gb300 import brm
+    dA = brm.to_device(A)
+    out = {}
+    for name, h in (("sort", False), ("hash", True)):
+        ms, tr = _traced(lambda: brm.brm_spgemm_symbolic(dA, dA, symbolic_hash=h), max(2, min(args.steps, 5)), 1)
+        out[name] = {"ms_per_call": ms, "phases_ms": {k: round(v[0], 3) for k, v in tr.items()}}
     return out
 
 

@@ -129,11 +129,14 @@ typedef struct {
  *   reg_num_direct 1 (default): with reg_perm, rows of 32-key register bins
  *                  (the top bin among them) read their products from B at
  *                  output time instead of staging them in shared memory;
- *   symbolic_hash  register bins count a row's distinct columns in the
- *                  symbolic pass with the numeric pass's sorting network on
- *                  bare columns (0, default) or by hashing into a
- *                  shared-memory table (1, the paper's symbolic method;
- *                  slower on GB300 because of shared-memory atomics); the
+ *   symbolic_hash  the symbolic pass counts a row's distinct columns by
+ *                  sorting (register bins: the numeric pass's sorting
+ *                  network on bare columns; warp and block bins: merge
+ *                  rounds on column indices) (0, default), or by hashing
+ *                  every column into a shared-memory open-addressing table of
+ *                  twice the bin's capacity (1, the paper's symbolic method,
+ *                  Section III-D-2); long rows always count their columns in a
+ *                  bitmap (a table whose hash is the column itself); the
  *                  counts are identical;
  *   warp_max_nprod other rows with 0 < nprod <= this (and <= as many lists)
  *                  are merged by one warp in shared memory (at most 256).

@@ -84,6 +84,113 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_rows_block(RowJob j) {
         brm_row<P, BlockGrp<kBlockThreads>, kBlockK, 4>(g, j.rows[r], j, b0, b1);
 }
 
+// ---------------------------------------------------------------------------
+// Symbolic pass of the warp and block bins by hashing (option symbolic_hash),
+// the paper's symbolic step (Section III-D-2, step 3): every column of the
+// row's lists goes into a shared-memory open-addressing table of twice the
+// bin's product capacity (multiplicative hash, linear probing, load factor
+// <= 1/2); the row's nnz is the number of first insertions.  The products
+// are spread evenly over the group: the list ends are prefix-summed first
+// and every thread finds the list of each of its positions.  (Long rows count
+// their columns in a bitmap: a table whose hash is the column itself and that
+// never collides.)
+// ---------------------------------------------------------------------------
+template <class G>
+__device__ __forceinline__ int hash_count_row(const G &g, const RowIn<float> &ri, int32_t *tab, int hs_bits,
+                                              int32_t *q0s, int32_t *offs) {
+    const int L = ri.L;
+    int carry = 0;
+    if (g.rank() == 0) offs[0] = 0;
+    for (int base = 0; base < L; base += G::N) {
+        const int t = base + g.rank();
+        int len = 0;
+        if (t < L) {
+            const int k = ri.acol[t];
+            const int q0 = ri.brp[k];
+            len = ri.brp[k + 1] - q0;
+            q0s[t] = q0;
+        }
+        int tot;
+        const int ex = g.scan_excl(len, tot);
+        if (t < L) offs[t + 1] = carry + ex + len;
+        carry += tot;
+    }
+    const int hs = 1 << hs_bits;
+    for (int x = g.rank(); x < hs; x += G::N) tab[x] = -1;
+    g.sync();
+    const int N = carry;
+    int cnt = 0;
+    for (int p = g.rank(); p < N; p += G::N) {
+        const int t = find_last_le(offs, L, p);
+        const int32_t c = __ldg(ri.bcol + q0s[t] + (p - offs[t]));
+        unsigned h = ((uint32_t)c * 0x9E3779B1u) >> (32 - hs_bits);
+        while (true) {
+            const int old = atomicCAS(tab + h, -1, c);
+            if (old == -1) { ++cnt; break; }
+            if (old == c) break;
+            h = (h + 1) & (unsigned)(hs - 1);
+        }
+    }
+    int total;
+    g.scan_excl(cnt, total);
+    return total;
+}
+
+constexpr int kHashWarpBits = 9;     // 512 slots: twice the warp bin's 256 products
+constexpr int kHashBlockBits = 13;   // 8192 slots: twice the block bin's 4096 products
+static_assert((1 << kHashWarpBits) >= 2 * kWarpCap && (1 << kHashBlockBits) >= 2 * kBlockCap, "load <= 1/2");
+
+__host__ __device__ constexpr size_t hash_grp_bytes(int bits, int lcap) {
+    return sizeof(int32_t) * ((size_t)(1 << bits) + 2 * (size_t)lcap + 1);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sym_hash_warp(RowJob j) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wid = threadIdx.x >> 5;
+    int32_t *tab = reinterpret_cast<int32_t *>(smem + (size_t)wid * hash_grp_bytes(kHashWarpBits, kWarpCap));
+    int32_t *q0s = tab + (1 << kHashWarpBits);
+    int32_t *offs = q0s + kWarpCap;
+    const WarpGrp g;
+    for (int r = blockIdx.x * kWarpsPerBlock + wid; r < j.count; r += gridDim.x * kWarpsPerBlock) {
+        const int row = j.rows[r];
+        const int n = hash_count_row(g, row_in<float>(j, row), tab, kHashWarpBits, q0s, offs);
+        if (g.rank() == 0 && j.out_cnt != nullptr) j.out_cnt[row] = n;
+        __syncwarp();
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlockThreads) k_sym_hash_block(RowJob j) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int ws[kBlockThreads / 32 + 1];
+    int32_t *tab = reinterpret_cast<int32_t *>(smem);
+    int32_t *q0s = tab + (1 << kHashBlockBits);
+    int32_t *offs = q0s + kBlockLCap;
+    BlockGrp<kBlockThreads> g;
+    g.ws = ws;
+    for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
+        const int row = j.rows[r];
+        const int n = hash_count_row(g, row_in<float>(j, row), tab, kHashBlockBits, q0s, offs);
+        if (threadIdx.x == 0 && j.out_cnt != nullptr) j.out_cnt[row] = n;
+        __syncthreads();
+    }
+}
+
+template <class K>
+cudaError_t launch_grp_kernel(K kern, int threads, size_t sm, int rows_per_block, const RowJob &j, cudaStream_t st,
+                              int sms) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, sm);
+    const int need = (j.count + rows_per_block - 1) / rows_per_block;
+    const int grid = max(1, min(need, sms * max(occ, 1)));
+    kern<<<grid, threads, sm, st>>>(j);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 // Arena layout of one long row with n products and L lists; host and device
 // both use it.  The value arrays hold max(n, L) entries because the
 // multiplying phase parks one A value per list in the spare buffer (a row may
@@ -157,6 +264,16 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
         return launch_reg_rows<P>(32, jt, st, sms);
     }
     if (bin >= kBinReg0 && bin < kBinReg0 + kNumRegBins) return launch_reg_rows<P>(reg_bin_tpr(bin), j, st, sms);
+    if constexpr (!P::kVal && !P::kPerm) {
+        // symbolic pass by hashing, on request
+        if (j.sym_hash && bin == kBinWarp)
+            return launch_grp_kernel(k_sym_hash_warp<PIdx>, kWarpsPerBlock * 32,
+                                     kWarpsPerBlock * hash_grp_bytes(kHashWarpBits, kWarpCap), kWarpsPerBlock, j, st,
+                                     sms);
+        if (j.sym_hash && bin == kBinBlock)
+            return launch_grp_kernel(k_sym_hash_block<PIdx>, kBlockThreads, hash_grp_bytes(kHashBlockBits, kBlockLCap), 1, j,
+                                     st, sms);
+    }
     if (bin == kBinWarp) {
         const size_t sm = kWarpsPerBlock * pair_bytes<P>(kWarpCap, kWarpCap);
         auto kern = k_rows_warp<P, kWarpCap>;

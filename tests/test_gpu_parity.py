@@ -209,6 +209,27 @@ def test_symbolic_and_row_nprod():
     assert tot == ref.sum() and mx == ref.max() and ml == np.diff(A.rp).max()
 
 
+def test_hash_symbolic_every_bin():
+    """The paper's hashing symbolic pass (register, warp and block bins by
+    shared-memory hash tables, long rows by the column bitmap) gives the
+    oracle's row counts, and BRMerge-Precise on them the oracle's C."""
+    R = I.rmat(14, 16, seed=87)
+    dR = brm.to_device(R)
+    want = np.concatenate(([0], np.cumsum(oracle.symbolic(R, R))))
+    brm.brm_trace_reset()
+    was = brm.brm_trace_enable(True)
+    rp, nnz = brm.brm_spgemm_symbolic(dR, dR, symbolic_hash=True)
+    t = brm.brm_trace_read()
+    brm.brm_trace_enable(was)
+    assert nnz == want[-1] and np.array_equal(rp.cpu().numpy(), want)
+    assert t["symbolic_warp"][1] == 1 and t["symbolic_block"][1] == 1 and t["symbolic_long"][1] >= 1
+    C = run(R, R, symbolic_hash=True)
+    nprod = oracle.row_nprod(R, R)
+    rows = np.sort(np.concatenate([np.argsort(-nprod, kind="stable")[:30],
+                                   np.nonzero((nprod > 256) & (nprod <= 4096))[0][:200]]))
+    assert_rows_exact(C, oracle.alg1(R, R, rows), rows)
+
+
 def test_validate_rejects_malformed():
     A = I.random_int(10, 10, 0.5, 3, 0)
     bad_col = A.col.copy()
