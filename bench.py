@@ -350,13 +350,18 @@ def run_gpu(args):
         if dist is not None:
             dist.barrier()
 
-    # every rank multiplies its own independent matrix (weak scaling)
+    # every rank multiplies its own independent matrix (weak scaling), or
+    # with --shard the ranks share one product by the static row split
+    # (strong scaling: each rank its rows of C, B whole on every rank, one
+    # all-gather of the ranks' nnz per step)
+    shard = args.shard and world > 1
+    seed = I.DEFAULT_SEED if shard else rank_seed(rank)
     if args.workload == "er":
-        A = I.erdos_renyi(1 << 20, 16, seed=rank_seed(rank))
+        A = I.erdos_renyi(1 << 20, 16, seed=seed)
         wname = ER_WORKLOAD
         phase = "numeric_reg"
     else:
-        A = I.rmat(args.scale, 16, seed=rank_seed(rank))
+        A = I.rmat(args.scale, 16, seed=seed)
         wname = workload_name(args.scale)
         phase = "numeric_long"
     vbytes = 8
@@ -364,13 +369,31 @@ def run_gpu(args):
     nprod_total = int(nprod.sum())
     dA = brm.to_device(A, device=f"cuda:{dev}")
     st = torch.cuda.current_stream()
+    if shard:
+        bounds = brm.brm_row_split(dA, dA, world)
+        r0, r1 = bounds[rank], bounds[rank + 1]
+        dL = brm.row_slice(dA, r0, r1)
+    else:
+        r0, r1 = 0, A.rows
+        dL = dA
+
+    def step(left):
+        Cx = brm.brm_spgemm_precise(left, dA if shard else left)
+        if shard:
+            brm.global_row_offset(Cx.nnz, None, Cx.rp.device)
+        return Cx
+
+    def value_of(ms_total, nsteps):
+        # whole-job GFLOP/s: weak -- every rank its own product; strong -- one product
+        return job_gflops(nprod_total, 1 if shard else world, nsteps, ms_total)
 
     # warm-up (also gives the result's row lengths)
     C = None
     for _ in range(args.warmup):
-        C = brm.brm_spgemm_precise(dA, dA)
+        C = step(dL)
     torch.cuda.synchronize()
-    row_nnz = np.diff(C.rp.cpu().numpy())
+    row_nnz = np.zeros(A.rows, dtype=np.int64)
+    row_nnz[r0:r1] = np.diff(C.rp.cpu().numpy())
     nnz_c = C.nnz
     del C
     torch.cuda.empty_cache()
@@ -385,7 +408,7 @@ def run_gpu(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        C = brm.brm_spgemm_precise(dA, dA)
+        C = step(dL)
         del C
     e1.record(st)
     torch.cuda.synchronize()
@@ -396,19 +419,26 @@ def run_gpu(args):
     brm.brm_trace_enable(False)
     clk = clocks.stop() if clocks else None
     ms_max = reduce_max(ms, dist, f"cuda:{dev}")
-    value = job_gflops(nprod_total, world, args.steps, ms_max)
+    value = value_of(ms_max, args.steps)
 
     # ---- end to end: host buffers, copies inside the timed region ----------
-    # A comes in from pinned host memory every step; all of C goes back to
-    # the host every step, through two pinned staging buffers used in turn
-    # (C is larger than is sensible to pin at once).
-    hA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-          for k, v in (("rp", A.rp.astype(np.int32)), ("col", A.col.astype(np.int32)), ("val", A.val))}
+    # the step's inputs come in from pinned host memory every step (A, or
+    # this rank's rows of A and the whole B); all of the step's C goes back
+    # to the host every step, through two pinned staging buffers used in
+    # turn (C is larger than is sensible to pin at once)
+    s0, s1 = int(A.rp[r0]), int(A.rp[r1])
+    host_in = [("rp", (A.rp[r0:r1 + 1].astype(np.int64) - s0).astype(np.int32)), ("col", A.col[s0:s1]),
+               ("val", A.val[s0:s1])]
+    if shard:
+        host_in += [("brp", A.rp.astype(np.int32)), ("bcol", A.col.astype(np.int32)), ("bval", A.val)]
+    hA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host_in}
+    dIn = {k: torch.empty_like(v, device=f"cuda:{dev}") for k, v in hA.items()}
     h2d = sum(t.numel() * t.element_size() for t in hA.values())
     stage_bytes = 1 << 30
     stages = [torch.empty(stage_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    d2h = (A.rows + 1) * 8 + nnz_c * (4 + vbytes)
-    dA2 = brm.DeviceCSR(A.rows, A.cols, torch.empty_like(dA.rp), torch.empty_like(dA.col), torch.empty_like(dA.val))
+    d2h = (r1 - r0 + 1) * 8 + nnz_c * (4 + vbytes)
+    dL2 = brm.DeviceCSR(r1 - r0, A.cols, dIn["rp"], dIn["col"], dIn["val"])
+    dB2 = brm.DeviceCSR(A.rows, A.cols, dIn["brp"], dIn["bcol"], dIn["bval"]) if shard else dL2
 
     def copy_out(t, k):
         b = t.view(torch.uint8).reshape(-1)
@@ -424,10 +454,11 @@ def run_gpu(args):
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(st)
     for _ in range(e_steps):
-        dA2.rp.copy_(hA["rp"], non_blocking=True)
-        dA2.col.copy_(hA["col"], non_blocking=True)
-        dA2.val.copy_(hA["val"], non_blocking=True)
-        C = brm.brm_spgemm_precise(dA2, dA2)
+        for k in hA:
+            dIn[k].copy_(hA[k], non_blocking=True)
+        C = brm.brm_spgemm_precise(dL2, dB2)
+        if shard:
+            brm.global_row_offset(C.nnz, None, C.rp.device)
         k = copy_out(C.rp, 0)
         k = copy_out(C.col, k)
         copy_out(C.val, k)
@@ -437,8 +468,8 @@ def run_gpu(args):
     e2e_ms = f0.elapsed_time(f1)
     barrier()
     e2e_ms = reduce_max(e2e_ms, dist, f"cuda:{dev}")
-    e2e_value = job_gflops(nprod_total, world, e_steps, e2e_ms)
-    del stages, hA, dA2
+    e2e_value = value_of(e2e_ms, e_steps)
+    del stages, hA, dIn, dL2, dB2
     torch.cuda.empty_cache()
 
     if rank != 0:
@@ -452,9 +483,11 @@ def run_gpu(args):
     else:
         L = np.diff(A.rp.astype(np.int64))
         mask = (nprod > 0) & (nprod <= 1024) & (L <= 256)
+    mask[:r0] = False        # this rank's rows (all of them without --shard)
+    mask[r1:] = False
     per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in trace.items() if v[1]}
     # the traffic figures are for the workloads the captures scaled to
-    tkey = phase if (args.workload == "er" or args.scale == 20) else None
+    tkey = phase if not shard and (args.workload == "er" or args.scale == 20) else None
     roof = roofline(per_step, phase, numeric_bytes(A, A, mask, row_nnz, vbytes), tkey)
     phases = {k: round(v[0], 4) for k, v in per_step.items()}
 
@@ -473,10 +506,13 @@ def run_gpu(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wname, "n": A.rows, "nnz_A": A.nnz, "nprod": nprod_total, "nnz_C": nnz_c,
-                   "global_batch": world, "parallelism": f"independent products x{world}",
+                   "global_batch": 1 if shard else world,
+                   "parallelism": (f"row split of one product over {world} GPUs" if shard
+                                   else f"independent products x{world}"),
                    "l2": "output larger than L2 every step; no flush"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e_steps},
@@ -732,6 +768,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--headline-only", action="store_true", help="skip the 'also' block")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split one product's rows over the ranks (strong scaling) instead of one "
+                         "independent product per rank")
     ap.add_argument("--profile", action="store_true", help="two calls only (for ncu captures)")
     ap.add_argument("--profile-n", type=int, default=1 << 20)
     ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "batched", "diff"],

@@ -304,9 +304,11 @@ int brm_spgemm_numeric_noalloc(const brm_csr *A, const brm_csr *B, const int64_t
  * A), dB_kj over the rows i in increasing order (one thread per entry of B,
  * after A's entries are bucketed by column and every bucket is sorted).
  * Returns BRM_ERR_INVALID if C's pattern misses a column.  Synchronises the
- * stream once.  opts is unused (may be NULL); alloc provides a 4-byte flag
- * and, when dB is computed, about 16 * A.cols + 8 * A.nnz bytes of
- * workspace.
+ * stream twice when dB is computed (the product count sizes its workspace),
+ * else once.  opts is unused (may be NULL); alloc provides a 4-byte flag
+ * and, when dB is computed, about 16 * A.cols + 32 * A.nnz bytes plus one
+ * value per intermediate product (every product's G_ij, kept by the dA pass
+ * for the dB sums) of workspace.
  */
 int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row_ptr, const int32_t *C_col_idx,
                         const void *dC, void *dA_val, void *dB_val, const brm_options *opts,
@@ -379,12 +381,30 @@ void brm_csr_out_free(brm_csr_out *C, const brm_allocator *alloc, void *stream);
 /*
  * Per-row statistics used by the binning (step 1 of both libraries, Section
  * III-D; the buffer sizing that opens Algorithm 1): nprod_i = sum over k in A_i* of |B_k*|.
- *   row_nprod   device int64[A.rows], caller-allocated.
+ *   row_nprod   device int64[A.rows], caller-allocated, or NULL (only the
+ *               totals below are wanted).
  *   total_nprod, max_row_nprod, max_row_nnz_A: host int64*, may be NULL.
  * Synchronises the stream once.
  */
 int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_t *total_nprod,
                   int64_t *max_row_nprod, int64_t *max_row_nnz_A, void *stream);
+
+/*
+ * The static split of the rows (Section III-D: the rows are cut into
+ * contiguous groups of about equal intermediate products, one per worker),
+ * used to shard one product over several GPUs: every GPU holds B, computes
+ * the rows bounds[p] .. bounds[p+1]-1 of C with its own call on that slice of
+ * A's rows, and one exchange of the parts' nnz places its rows in the global
+ * row pointer.
+ *   parts   number of parts (>= 1).
+ *   bounds  host int64[parts + 1], written: bounds[0] = 0, bounds[parts] =
+ *           A.rows, non-decreasing; part p starts at the first row whose
+ *           products before it reach floor(p * total_nprod / parts).
+ * Workspace (nprod per row, its prefix sum) comes from alloc.  Synchronises
+ * the stream once.
+ */
+int brm_row_split(const brm_csr *A, const brm_csr *B, int32_t parts, int64_t *bounds, const brm_allocator *alloc,
+                  void *stream);
 
 /*
  * Tracing (the measurement side of the paper's evaluation, Section IV-A: the

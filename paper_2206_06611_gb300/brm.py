@@ -100,6 +100,8 @@ def load(build_if_needed: bool = True):
     lib.brm_csr_out_free.argtypes = [pout, pal, P]
     lib.brm_csr_out_free.restype = None
     lib.brm_row_nprod.argtypes = [pcsr, pcsr, P, P, P, P, P]
+    lib.brm_row_split.argtypes = [pcsr, pcsr, ctypes.c_int32, P, pal, P]
+    lib.brm_row_split.restype = ctypes.c_int
     lib.brm_spgemm_numeric_noalloc.argtypes = [pcsr, pcsr, P, P, P, popt, P]
     lib.brm_spgemm_backward.argtypes = [pcsr, pcsr, P, P, P, P, P, popt, pal, P]
     lib.brm_spgemm_backward.restype = ctypes.c_int
@@ -530,6 +532,56 @@ def brm_row_nprod(A: DeviceCSR, B: DeviceCSR, *, stream=None):
     _check(lib.brm_row_nprod(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(out.data_ptr()), ctypes.byref(tot),
                              ctypes.byref(mx), ctypes.byref(ml), _stream(stream)))
     return out[:A.rows], int(tot.value), int(mx.value), int(ml.value)
+
+
+# ---------------------------------------------------------------------------
+# one product over several GPUs: the static row split
+# ---------------------------------------------------------------------------
+def brm_row_split(A: DeviceCSR, B: DeviceCSR, parts: int, *, stream=None) -> list:
+    """Row bounds (parts + 1 ints) of the nprod-balanced static split."""
+    lib = load()
+    a, b = _csr_struct(A), _csr_struct(B)
+    out = (ctypes.c_int64 * (parts + 1))()
+    _check(lib.brm_row_split(ctypes.byref(a), ctypes.byref(b), int(parts), ctypes.cast(out, ctypes.c_void_p),
+                             ctypes.byref(_allocator().struct), _stream(stream)))
+    return list(out)
+
+
+def row_slice(A: DeviceCSR, r0: int, r1: int) -> DeviceCSR:
+    """Rows r0 .. r1-1 of A as a CSR of their own (row pointer rebased to 0;
+    columns and values are views of A's)."""
+    s, e = int(A.rp[r0].item()), int(A.rp[r1].item())
+    rp = (A.rp[r0:r1 + 1] - s).to(A.rp.dtype)
+    return DeviceCSR(r1 - r0, A.cols, rp, A.col[s:e], None if A.val is None else A.val[s:e])
+
+
+def global_row_offset(nnz_local: int, group=None, device=None) -> tuple:
+    """(offset of this rank's rows in C's global arrays, global nnz): one
+    all-gather of every rank's nnz (int64) over torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    t = torch.tensor([int(nnz_local)], dtype=torch.int64, device=device)
+    parts = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(parts, t, group=group)
+    counts = [int(x.item()) for x in parts]
+    return sum(counts[:rank]), sum(counts)
+
+
+def spgemm_sharded(A: DeviceCSR, B: DeviceCSR, group=None, **opts):
+    """This rank's share of C = A * B over the ranks of a process group: the
+    rows (r0, r1) of the static split, computed by BRMerge-Precise on that
+    slice of A (B whole on every rank), and their place in the global C.
+    Returns (C rows as a DeviceCSR with a local row pointer, r0, r1, offset
+    of the rows' entries in the global C, global nnz)."""
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    bounds = brm_row_split(A, B, world)
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    C = brm_spgemm_precise(row_slice(A, r0, r1), B, **opts)
+    dev = C.rp.device if dist.get_backend(group) == "nccl" else "cpu"
+    off, total = global_row_offset(C.nnz, group, dev)
+    return C, r0, r1, off, total
 
 
 # ---------------------------------------------------------------------------

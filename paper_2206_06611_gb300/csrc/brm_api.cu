@@ -1277,13 +1277,40 @@ int brm_spgemm_backward(const brm_csr *A, const brm_csr *B, const int64_t *C_row
     a.kb = B->rows;
     a.nnz_b = B->nnz;
     if (dB_val && B->nnz > 0 && A->nnz > 0) {
-        // A^T's rows for the ordered dB sums
+        // A^T's rows for the ordered dB sums, and every product's G_ij
+        int64_t nprod = 0;
+        {
+            BinStats *bs;
+            if ((rc = get(mem, bs, 1, "statistics"))) return rc;
+            BRM_CUDA(cudaMemsetAsync(bs, 0, sizeof(BinStats), st));
+            BinArgs ba{};
+            ba.m = A->rows;
+            ba.arp = A->row_ptr;
+            ba.acol = A->col_idx;
+            ba.brp = B->row_ptr;
+            ba.reg_keys = kRegKeysDefault;
+            ba.warp_cap = kWarpCap;
+            ba.block_cap = kBlockCap;
+            ba.block_lcap = kBlockLCap;
+            ba.st = bs;
+            BRM_CUDA(launch_bin(ba, st));
+            BinStats h{};
+            BRM_CUDA(cudaMemcpyAsync(&h, bs, sizeof h, cudaMemcpyDeviceToHost, st));
+            BRM_CUDA(cudaStreamSynchronize(st));
+            nprod = (int64_t)h.total_nprod;
+            mem.free_one(bs);
+        }
         const size_t ka = (size_t)std::max<int64_t>(A->cols, 1);
         if ((rc = get(mem, a.ws_cnt, ka, "backward column counts"))) return rc;
         if ((rc = get(mem, a.ws_colptr, ka + 1, "backward column starts"))) return rc;
         if (!(a.ws_scan = mem.get(scan_tmp_bytes(A->cols)))) return fail(BRM_ERR_OOM, "backward scan workspace");
+        if (!(a.ws_scan2 = mem.get(scan_tmp_bytes(A->nnz)))) return fail(BRM_ERR_OOM, "backward scan workspace");
         if ((rc = get(mem, a.ws_ent, (size_t)A->nnz, "backward column entries"))) return rc;
         if ((rc = get(mem, a.ws_row, (size_t)A->nnz, "backward entry rows"))) return rc;
+        if ((rc = get(mem, a.ws_plen, (size_t)A->nnz, "backward product counts"))) return rc;
+        if ((rc = get(mem, a.ws_poff, (size_t)A->nnz + 1, "backward product offsets"))) return rc;
+        if (!(a.ws_gp = mem.get((size_t)std::max<int64_t>(nprod, 1) * value_bytes(A->dtype))))
+            return fail(BRM_ERR_OOM, "backward per-product gradients (%lld values)", (long long)nprod);
     } else if (dB_val && B->nnz > 0) {
         BRM_CUDA(cudaMemsetAsync(dB_val, 0, (size_t)B->nnz * value_bytes(A->dtype), st));   // A has no entries
         dB_val = nullptr;
@@ -1326,7 +1353,6 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
     g_err.clear();
     int rc = check_pair(A, B, false);
     if (rc) return rc;
-    if (!row_nprod && A->rows > 0) return fail(BRM_ERR_INVALID, "row_nprod is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Mem mem(nullptr, st);
     BinStats *bs;
@@ -1354,6 +1380,49 @@ int brm_row_nprod(const brm_csr *A, const brm_csr *B, int64_t *row_nprod, int64_
     if (total_nprod) *total_nprod = (int64_t)h.total_nprod;
     if (max_row_nprod) *max_row_nprod = (int64_t)h.max_nprod;
     if (max_row_nnz_A) *max_row_nnz_A = (int64_t)h.max_L;
+    g_trace.flush();
+    return BRM_OK;
+}
+
+int brm_row_split(const brm_csr *A, const brm_csr *B, int32_t parts, int64_t *bounds, const brm_allocator *alloc,
+                  void *stream) {
+    g_err.clear();
+    int rc = check_pair(A, B, false);
+    if (rc) return rc;
+    if (parts < 1) return fail(BRM_ERR_INVALID, "parts must be at least 1 (got %d)", parts);
+    if (!bounds) return fail(BRM_ERR_INVALID, "bounds is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t m = A->rows;
+    Mem mem(alloc, st);
+    BinStats *bs;
+    int64_t *nprod, *excl, *db;
+    if ((rc = get(mem, bs, 1, "statistics"))) return rc;
+    if ((rc = get(mem, nprod, (size_t)std::max<int64_t>(m, 1), "row nprod"))) return rc;
+    if ((rc = get(mem, excl, (size_t)m + 1, "product prefix"))) return rc;
+    if ((rc = get(mem, db, (size_t)parts + 1, "bounds"))) return rc;
+    void *tmp = mem.get(scan_tmp_bytes(m));
+    if (!tmp) return fail(BRM_ERR_OOM, "scan workspace");
+    BRM_CUDA(cudaMemsetAsync(bs, 0, sizeof(BinStats), st));
+    BinArgs a{};
+    a.m = m;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.brp = B->row_ptr;
+    a.reg_keys = kRegKeysDefault;
+    a.warp_cap = kWarpCap;
+    a.block_cap = kBlockCap;
+    a.block_lcap = kBlockLCap;
+    a.nprod = nprod;
+    a.st = bs;
+    {
+        PhaseScope ps(kPhBin, st);
+        if (m > 0) BRM_CUDA(launch_bin(a, st));
+        BRM_CUDA(launch_scan(nprod, excl, m, tmp, st));
+        BRM_CUDA(launch_row_split(excl, m, parts, db, st));
+    }
+    BRM_CUDA(cudaMemcpyAsync(bounds, db, ((size_t)parts + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BRM_CUDA(cudaStreamSynchronize(st));
+    for (int32_t p = 1; p <= parts; ++p) bounds[p] = std::max(bounds[p], bounds[p - 1]);
     g_trace.flush();
     return BRM_OK;
 }

@@ -14,12 +14,15 @@
 // where the previous one ended.
 // dB: every entry of B sums its terms over the rows i in increasing order,
 // sequentially, so the result is deterministic and the same as a plain loop
-// over the rows.  That needs, for every column k of A, its entries in row
+// over the rows.  The dA pass stores every product's G_ij on the way (at the
+// product's place in A's entry order), so a term is two loads.  That needs, for every column k of A, its entries in row
 // order (A^T's rows): they are bucketed by column (a count, a prefix sum and
 // an atomic scatter of the entry indices), and every bucket is then sorted --
 // an entry index grows with the row, so sorting the indices orders the rows.
 // A bucket of at most 1024 entries is sorted by one warp in registers, a
-// longer one by a thread block in device memory.
+// longer one by a thread block in device memory.  An entry of B sums its
+// bucket alone when the bucket is short, with a warp forming 32 terms at a
+// time when it is long.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -50,6 +53,15 @@ __device__ __forceinline__ int64_t row_of_entry(const int32_t *__restrict__ arp,
     return lo;
 }
 
+// Products of every entry of A: plen[p] = |B_k*| for its column k.
+__global__ void __launch_bounds__(256) k_bwd_plen(BackwardArgs a, int64_t *plen) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.nnz_a;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int k = a.acol[p];
+        plen[p] = a.brp[k + 1] - a.brp[k];
+    }
+}
+
 // Bucket sizes: cnt[k] = entries of A in column k; row_of[p] = the row of entry p.
 __global__ void __launch_bounds__(256) k_bwd_count(BackwardArgs a, unsigned long long *cnt, int32_t *row_of) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.nnz_a;
@@ -67,24 +79,51 @@ __global__ void __launch_bounds__(256) k_bwd_scatter(BackwardArgs a, unsigned lo
 }
 
 // Sorts every bucket of at most 1024 entries, one warp per bucket: the
-// indices as keys of the register bitonic network (32 lanes x 32 keys).
+// indices as keys of a bitonic network sized to the bucket (one key per lane
+// up to 32 entries, else the register network of 32 lanes x 8, 16 or 32
+// keys).
+template <int E>
+__device__ __forceinline__ void bwd_sort_warp(int32_t *e, int64_t n, int lane) {
+    uint32_t key[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int64_t q = (int64_t)i * 32 + lane;
+        key[i] = q < n ? (uint32_t)e[q] : kKeyPad;
+    }
+    reg_bitonic_sort<32, E>(key, lane);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int64_t q = (int64_t)lane * E + i;
+        if (q < n) e[q] = (int32_t)key[i];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bwd_sort_small(const int64_t *colptr, int64_t ncols, int32_t *ent) {
+    constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < ncols; k += warps) {
         const int64_t b = colptr[k], n = colptr[k + 1] - b;
         if (n < 2 || n > 1024) continue;
-        uint32_t key[32];
+        if (n <= 32) {
+            // one key per lane: lane x ends with the x-th smallest
+            uint32_t key = lane < n ? (uint32_t)ent[b + lane] : kKeyPad;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int64_t q = (int64_t)i * 32 + lane;
-            key[i] = q < n ? (uint32_t)ent[b + q] : kKeyPad;
-        }
-        reg_bitonic_sort<32, 32>(key, lane);
+            for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int64_t q = (int64_t)lane * 32 + i;
-            if (q < n) ent[b + q] = (int32_t)key[i];
+                for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                    const uint32_t o = __shfl_xor_sync(kFull, key, jj);
+                    const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+                    key = (up == low) ? min(key, o) : max(key, o);
+                }
+            }
+            if (lane < n) ent[b + lane] = (int32_t)key;
+        } else if (n <= 256) {
+            bwd_sort_warp<8>(ent + b, n, lane);
+        } else if (n <= 512) {
+            bwd_sort_warp<16>(ent + b, n, lane);
+        } else {
+            bwd_sort_warp<32>(ent + b, n, lane);
         }
     }
 }
@@ -120,31 +159,58 @@ __global__ void __launch_bounds__(1024) k_bwd_sort_big(const int64_t *colptr, in
     }
 }
 
-// dB_kj: one thread per entry q = (k, j) of B, the terms A_ik * G_ij summed
-// over the bucket of column k in order (rows increasing), from zero.
+// Buckets longer than this are summed by the warps of a block per row of B.
+constexpr int64_t kBwdWarpCol = 64;
+
+// The term A_ik * G_ij of bucket entry p (an entry (i, k) of A) for the jj-th
+// entry of B_k*: G_ij was stored per product by the dA pass.
 template <class V>
-__global__ void __launch_bounds__(256) k_bwd_db(BackwardArgs a, const int64_t *colptr, const int32_t *ent,
-                                                const int32_t *row_of, int64_t nnz_b) {
-    const V *aval = static_cast<const V *>(a.aval);
-    const V *g = static_cast<const V *>(a.dC);
+__device__ __forceinline__ V bwd_term(const BackwardArgs &a, int32_t p, int jj) {
+    return __ldg(static_cast<const V *>(a.aval) + p) * static_cast<const V *>(a.ws_gp)[a.ws_poff[p] + jj];
+}
+
+// dB_kj: one thread per entry q = (k, j) of B whose bucket (column k of A)
+// has at most kBwdWarpCol entries, the terms A_ik * G_ij summed over the
+// bucket in order (rows increasing), from zero.
+template <class V>
+__global__ void __launch_bounds__(256) k_bwd_db(BackwardArgs a, const int64_t *colptr, const int32_t *ent) {
     V *db = static_cast<V *>(a.dB);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz_b;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.nnz_b;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = row_of_entry(a.brp, a.kb, q);
-        const int32_t j = __ldg(a.bcol + q);
+        const int64_t e0 = colptr[k], e1 = colptr[k + 1];
+        if (e1 - e0 > kBwdWarpCol) continue;
+        const int jj = (int)(q - a.brp[k]);
         V acc = V(0);
-        for (int64_t e = colptr[k]; e < colptr[k + 1]; ++e) {
-            const int32_t p = ent[e];
-            const int32_t i = row_of[p];
-            const int64_t c0 = a.crp[i], c1 = a.crp[i + 1];
-            const int64_t w = lower_bound_col(a.ccol, c0, c1, j);
-            if (w >= c1 || __ldg(a.ccol + w) != j) {
-                atomicOr(a.err, 1u);   // C's pattern is not the one of A * B
-                break;
-            }
-            acc += __ldg(aval + p) * __ldg(g + w);
-        }
+        for (int64_t e = e0; e < e1; ++e) acc += bwd_term<V>(a, ent[e], jj);
         db[q] = acc;
+    }
+}
+
+// dB for the rows k of B whose bucket has more than kBwdWarpCol entries: one
+// thread block per row, its warps taking the row's entries in turn; for an
+// entry the lanes form 32 terms at a time and every lane adds them in bucket
+// order, so the sum is the same sequential sum as above.
+template <class V>
+__global__ void __launch_bounds__(256) k_bwd_db_warp(BackwardArgs a, const int64_t *colptr, const int32_t *ent) {
+    constexpr unsigned kFull = 0xffffffffu;
+    V *db = static_cast<V *>(a.dB);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t k = blockIdx.x; k < a.kb; k += gridDim.x) {
+        const int64_t e0 = colptr[k], e1 = colptr[k + 1];
+        if (e1 - e0 <= kBwdWarpCol) continue;
+        const int q0 = a.brp[k], q1 = a.brp[k + 1];
+        for (int q = q0 + wid; q < q1; q += nw) {
+            const int jj = q - q0;
+            V acc = V(0);
+            for (int64_t eb = e0; eb < e1; eb += 32) {
+                const int64_t e = eb + lane;
+                const V t = e < e1 ? bwd_term<V>(a, ent[e], jj) : V(0);
+                const int n = (int)min((int64_t)32, e1 - eb);
+                for (int l = 0; l < n; ++l) acc += __shfl_sync(kFull, t, l);
+            }
+            if (lane == 0) db[q] = acc;
+        }
     }
 }
 
@@ -153,6 +219,7 @@ __global__ void __launch_bounds__(256) k_backward(BackwardArgs a) {
     const V *bval = static_cast<const V *>(a.bval);
     const V *g = static_cast<const V *>(a.dC);
     V *da = static_cast<V *>(a.dA);
+    V *gp = static_cast<V *>(a.ws_gp);
     const int64_t nnz = a.nnz_a;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -170,6 +237,7 @@ __global__ void __launch_bounds__(256) k_backward(BackwardArgs a) {
             }
             const V gij = __ldg(g + lo);
             acc += gij * __ldg(bval + q);
+            if (gp) gp[a.ws_poff[p] + (q - a.brp[k])] = gij;
             ++lo;
         }
         if (da) da[p] = acc;
@@ -186,13 +254,20 @@ cudaError_t launch_backward(const BackwardArgs &a, bool f64, cudaStream_t st) {
     const int T = 256;
     auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + T - 1) / T, (int64_t)sms * 32)); };
     cudaError_t e;
-    if (a.dA) {
+    const bool want_db = a.dB && a.nnz_b > 0;
+    if (want_db) {
+        // where every entry of A keeps the G_ij of its products
+        k_bwd_plen<<<grid_for(a.nnz_a), T, 0, st>>>(a, a.ws_plen);
+        if ((e = launch_scan(a.ws_plen, a.ws_poff, a.nnz_a, a.ws_scan2, st)) != cudaSuccess) return e;
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (a.dA || want_db) {
         if (f64) k_backward<double><<<grid_for(a.nnz_a), T, 0, st>>>(a);
         else k_backward<float><<<grid_for(a.nnz_a), T, 0, st>>>(a);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (a.dB && a.nnz_b > 0) {
+    if (want_db) {
         // A^T's rows: bucket sizes, their prefix sum, scatter, sort
         if ((e = cudaMemsetAsync(a.ws_cnt, 0, (size_t)a.ka * sizeof(unsigned long long), st)) != cudaSuccess) return e;
         k_bwd_count<<<grid_for(a.nnz_a), T, 0, st>>>(a, reinterpret_cast<unsigned long long *>(a.ws_cnt), a.ws_row);
@@ -204,9 +279,12 @@ cudaError_t launch_backward(const BackwardArgs &a, bool f64, cudaStream_t st) {
         const int gw = (int)std::max<int64_t>(1, std::min<int64_t>((a.ka + 7) / 8, (int64_t)sms * 16));
         k_bwd_sort_small<<<gw, T, 0, st>>>(a.ws_colptr, a.ka, a.ws_ent);
         k_bwd_sort_big<<<std::max(sms, 1), 1024, 0, st>>>(a.ws_colptr, a.ka, a.ws_ent);
-        if (f64) k_bwd_db<double><<<grid_for(a.nnz_b), T, 0, st>>>(a, a.ws_colptr, a.ws_ent, a.ws_row, a.nnz_b);
-        else k_bwd_db<float><<<grid_for(a.nnz_b), T, 0, st>>>(a, a.ws_colptr, a.ws_ent, a.ws_row, a.nnz_b);
-        g_launches.fetch_add(6, std::memory_order_relaxed);
+        if (f64) k_bwd_db<double><<<grid_for(a.nnz_b), T, 0, st>>>(a, a.ws_colptr, a.ws_ent);
+        else k_bwd_db<float><<<grid_for(a.nnz_b), T, 0, st>>>(a, a.ws_colptr, a.ws_ent);
+        const int gwb = (int)std::max<int64_t>(1, std::min<int64_t>(a.kb, (int64_t)sms * 8));
+        if (f64) k_bwd_db_warp<double><<<gwb, T, 0, st>>>(a, a.ws_colptr, a.ws_ent);
+        else k_bwd_db_warp<float><<<gwb, T, 0, st>>>(a, a.ws_colptr, a.ws_ent);
+        g_launches.fetch_add(7, std::memory_order_relaxed);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

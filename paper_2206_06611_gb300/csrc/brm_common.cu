@@ -418,4 +418,30 @@ int long_win_grid(VKind v) {
     }
 }
 
+// The static split of Section III-D: bounds[p] = the first row whose
+// exclusive product prefix reaches floor(p * total / parts), bounds[parts] = m.
+__global__ void k_row_split(const int64_t *excl, int64_t m, int32_t parts, int64_t *bounds) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > parts) return;
+    if (p == parts) {
+        bounds[p] = m;
+        return;
+    }
+    const int64_t total = excl[m];
+    const int64_t target = (int64_t)(((__int128)total * p) / parts);
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (excl[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    bounds[p] = lo;
+}
+
+cudaError_t launch_row_split(const int64_t *excl, int64_t m, int32_t parts, int64_t *bounds, cudaStream_t st) {
+    const int T = 256;
+    k_row_split<<<(parts + T) / T, T, 0, st>>>(excl, m, parts, bounds);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 }  // namespace brm

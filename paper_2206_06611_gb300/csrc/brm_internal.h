@@ -176,6 +176,9 @@ cudaError_t launch_validate(int64_t rows, int64_t cols, int64_t nnz, const int32
 // scan_tmp_bytes(n)
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_scan(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t st);
+// bounds[0 .. parts] of the static nprod-balanced row split from the
+// exclusive product prefix excl[0 .. m]
+cudaError_t launch_row_split(const int64_t *excl, int64_t m, int32_t parts, int64_t *bounds, cudaStream_t st);
 // Upper: copy rows of C_bar (at cbar_off[i], row_size[i] long) to C at rp[i]
 cudaError_t launch_compact(int64_t m, const int64_t *cbar_off, const int64_t *rp, const int32_t *cbar_col,
                            const void *cbar_val, int32_t *col, void *val, size_t vbytes, cudaStream_t st);
@@ -189,11 +192,14 @@ struct BackwardArgs {
     const int64_t *crp; const int32_t *ccol; const void *dC;
     void *dA, *dB;            // either may be null
     unsigned int *err;        // set when C's pattern lacks a column of some B_k*
-    // dB workspace (backward_ws_bytes): bucket sizes / cursors (ka), bucket
-    // starts (ka + 1), the scan's temporary, entry indices and rows (nnz_a)
+    // dB workspace: bucket sizes / cursors (ka), bucket starts (ka + 1), the
+    // scans' temporaries, entry indices and rows (nnz_a), every entry's first
+    // product (nnz_a + 1) and every product's G_ij (nprod values)
     int64_t *ws_cnt, *ws_colptr;
-    void *ws_scan;
+    void *ws_scan, *ws_scan2;
     int32_t *ws_ent, *ws_row;
+    int64_t *ws_plen, *ws_poff;
+    void *ws_gp;
 };
 cudaError_t launch_backward(const BackwardArgs &a, bool f64, cudaStream_t st);
 

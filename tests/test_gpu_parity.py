@@ -219,10 +219,13 @@ def test_hash_symbolic_every_bin():
     brm.brm_trace_reset()
     was = brm.brm_trace_enable(True)
     rp, nnz = brm.brm_spgemm_symbolic(dR, dR, symbolic_hash=True)
+    assert nnz == want[-1] and np.array_equal(rp.cpu().numpy(), want)
+    # without the register bins, the short rows take the warp bin's table
+    rp, nnz = brm.brm_spgemm_symbolic(dR, dR, symbolic_hash=True, reg_max_nprod=-1)
     t = brm.brm_trace_read()
     brm.brm_trace_enable(was)
     assert nnz == want[-1] and np.array_equal(rp.cpu().numpy(), want)
-    assert t["symbolic_warp"][1] == 1 and t["symbolic_block"][1] == 1 and t["symbolic_long"][1] >= 1
+    assert t["symbolic_warp"][1] >= 1 and t["symbolic_block"][1] >= 1 and t["symbolic_long"][1] >= 1
     C = run(R, R, symbolic_hash=True)
     nprod = oracle.row_nprod(R, R)
     rows = np.sort(np.concatenate([np.argsort(-nprod, kind="stable")[:30],

@@ -49,3 +49,29 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.reduce_max(3.5, None, "cpu") == 3.5
     assert bench.job_gflops(10, 1, 1, 1.0) == pytest.approx(2e-5)
+
+
+def _offset_worker(rank, world, port, out):
+    from paper_2206_06611_gb300 import brm
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nnz = [7, 0, 123456789012][rank]              # int64 counts, one rank empty
+        out[rank] = brm.global_row_offset(nnz, None, "cpu")
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_shards_find_their_global_offsets(world):
+    """Row-sharded products (the static split of Section III-D over GPUs):
+    every rank learns where its rows' entries start in the global C, and the
+    global nnz, from one all-gather of the ranks' nnz."""
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_offset_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    counts = [7, 0, 123456789012][:world]
+    for r in range(world):
+        assert res[r] == (sum(counts[:r]), sum(counts))
