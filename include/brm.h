@@ -365,12 +365,15 @@ int brm_batch_take(brm_batch *batch, brm_csr_out *C, int64_t *row_offset);
 void brm_batch_destroy(brm_batch *batch);
 
 /*
- * Autotuner of the row bins: times brm_batch_create + brm_batch_numeric for
- * every candidate shape of the register bins (reg_keys 8, 16, 32 x reg_warps
- * 2, 4, 8; the other fields are taken from base) on the given products and
- * writes the fastest options to best (and its time in milliseconds to
- * best_ms, if not NULL).  Each candidate runs once to warm up and twice
- * timed (the minimum counts).  Synchronises the stream many times.
+ * Autotuner of the row bins: times brm_batch_create + brm_batch_numeric +
+ * brm_batch_check (wall clock; each candidate runs once to warm up and twice
+ * timed, the minimum counts) on the given products, first for every shape of
+ * the register bins (reg_keys 8, 16, 32 x reg_warps 2, 4, 8, each with its
+ * full register range), then for the bin thresholds one at a time from the
+ * best so far: reg_max_nprod at 1/2 and 1/4 of that range, reg_top switched,
+ * warp_max_nprod 128 and 64, block_max_nprod 2048 and 1024 (the other fields
+ * are taken from base).  Writes the fastest options to best (and its time in
+ * milliseconds to best_ms, if not NULL).  Synchronises the stream many times.
  */
 int brm_autotune(int32_t count, const brm_csr *A, const brm_csr *B, const brm_options *base, brm_options *best,
                  double *best_ms, const brm_allocator *alloc, void *stream);

@@ -1516,8 +1516,37 @@ int brm_autotune(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
     if (!best) return fail(BRM_ERR_INVALID, "best is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const brm_options b0 = resolve(base);
+    // wall time of create + numeric + check, the best of two runs after one
+    auto measure = [&](const brm_options &o, double &ms) -> int {
+        ms = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            BRM_CUDA(cudaStreamSynchronize(st));
+            const auto t0 = std::chrono::steady_clock::now();
+            brm_batch *b = nullptr;
+            int rc = batch_create(count, A, B, &o, alloc, st, &b);
+            if (!rc) rc = batch_numeric(b, st, false);
+            if (!rc) rc = batch_check(b, st);
+            const auto t1 = std::chrono::steady_clock::now();
+            delete b;
+            if (rc) return rc;
+            if (rep > 0) ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        }
+        return BRM_OK;
+    };
     double top = 1e300;
     brm_options win = b0;
+    auto consider = [&](brm_options o) -> int {
+        o = resolve(&o);
+        double ms;
+        const int rc = measure(o, ms);
+        if (rc) return rc;
+        if (ms < top) {
+            top = ms;
+            win = o;
+        }
+        return BRM_OK;
+    };
+    // 1. the register bins' shape: keys per thread x warps per block
     static const int kKeys[] = {8, 16, 32};
     static const int kWarps[] = {2, 4, 8};
     for (int keys : kKeys)
@@ -1526,24 +1555,45 @@ int brm_autotune(int32_t count, const brm_csr *A, const brm_csr *B, const brm_op
             o.reg_keys = keys;
             o.reg_warps = warps;
             o.reg_max_nprod = 0;   // the full register range of this shape
-            double ms = 1e300;
-            for (int rep = 0; rep < 3; ++rep) {
-                BRM_CUDA(cudaStreamSynchronize(st));
-                const auto t0 = std::chrono::steady_clock::now();
-                brm_batch *b = nullptr;
-                int rc = batch_create(count, A, B, &o, alloc, st, &b);
-                if (!rc) rc = batch_numeric(b, st, false);
-                if (!rc) rc = batch_check(b, st);
-                const auto t1 = std::chrono::steady_clock::now();
-                delete b;
-                if (rc) return rc;
-                if (rep > 0) ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
-            }
-            if (ms < top) {
-                top = ms;
-                win = resolve(&o);
-            }
+            int rc = consider(o);
+            if (rc) return rc;
         }
+    // 2. the bin thresholds, one at a time from the best so far: how far the
+    // register bins reach, the top register bin, the warp and block bins' sizes
+    {
+        const brm_options w = win;
+        const int full = kRegMaxTpr * w.reg_keys;
+        for (int cap : {full / 2, full / 4}) {
+            brm_options o = w;
+            o.reg_max_nprod = cap;
+            int rc = consider(o);
+            if (rc) return rc;
+        }
+    }
+    {
+        brm_options o = win;
+        o.reg_top = o.reg_top ? 0 : 1;
+        int rc = consider(o);
+        if (rc) return rc;
+    }
+    {
+        const brm_options w = win;
+        for (int wcap : {128, 64}) {
+            brm_options o = w;
+            o.warp_max_nprod = wcap;
+            int rc = consider(o);
+            if (rc) return rc;
+        }
+    }
+    {
+        const brm_options w = win;
+        for (int bcap : {2048, 1024}) {
+            brm_options o = w;
+            o.block_max_nprod = bcap;
+            int rc = consider(o);
+            if (rc) return rc;
+        }
+    }
     *best = win;
     if (best_ms) *best_ms = top;
     return BRM_OK;

@@ -101,6 +101,10 @@ def test_autotune_options_give_the_same_result():
     dev = [brm.to_device(M) for M in mats]
     opts, ms = brm.brm_autotune(dev, dev)
     assert ms > 0 and opts["reg_keys"] in (8, 16, 32) and 1 <= opts["reg_warps"] <= 8
+    # the thresholds come from the second stage's candidates
+    full = 32 * opts["reg_keys"]
+    assert opts["reg_max_nprod"] in (full, full // 2, full // 4)
+    assert opts["warp_max_nprod"] in (256, 128, 64) and opts["block_max_nprod"] in (4096, 2048, 1024)
     C, off = brm.brm_spgemm_batched(dev, dev, **opts)
     _check_products(C, off, mats, "f64", np.float64)
 
