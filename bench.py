@@ -750,10 +750,11 @@ def run_profile(args):
         A = I.rmat(args.scale, 16) if args.workload == "rmat" else I.erdos_renyi(args.profile_n, 16)
         dA = brm.to_device(A, device="cuda:0")
         for _ in range(2):
-            C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket)
+            C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket, long_window=args.long_window)
             torch.cuda.synchronize()
             del C
-        info = {"profile": args.workload, "n": A.rows, "long_bucket": args.long_bucket}
+        info = {"profile": args.workload, "n": A.rows, "long_bucket": args.long_bucket,
+                "long_window": args.long_window}
     info["launches"] = brm.brm_kernel_launches()
     print(json.dumps(info), flush=True)
 
@@ -780,6 +781,8 @@ def main():
                     help="--profile --workload batched: products of the mix (the first of the 512)")
     ap.add_argument("--long-bucket", action="store_true",
                     help="--profile: long rows' numeric pass by column buckets (option long_bucket)")
+    ap.add_argument("--long-window", action="store_true",
+                    help="--profile: long rows by column tiles (option long_window)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -290,7 +290,16 @@ struct Plan {
     std::vector<int32_t> long_rows_h;   // host copies, same order
     std::vector<int64_t> long_nprod_h;
     std::vector<int32_t> long_L_h;
+    // with column tiles: the long slots [0, long_split) keep the merge rounds
+    // (rows of more than kTileMaxL lists), the others take the tiles
+    int64_t long_split = 0;
 };
+
+// Whether the long rows of a product take the column tiles (brm_long_win.cuh):
+// the option is on, the bucket option off, and B has at most 2^24 columns.
+bool tiles_apply(const brm_options &o, int64_t bcols) {
+    return o.long_window && !o.long_bucket && bcols <= kLbMaxCols;
+}
 
 int validate_inputs(Mem &mem, const brm_csr *A, const brm_csr *B) {
     BinStats *st;
@@ -375,10 +384,19 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
         BRM_CUDA(cudaMemcpyAsync(np.data(), pl.long_nprod, nl * sizeof(int64_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaMemcpyAsync(Ls.data(), pl.long_L, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaStreamSynchronize(mem.st));
-        // largest rows first, so that the longest merges start earliest
+        // largest rows first, so that the longest merges start earliest; with
+        // column tiles, the rows of more than kTileMaxL lists (merge rounds)
+        // before the others
+        const bool tiles = tiles_apply(o, src.bcols);
         std::vector<int64_t> idx(nl);
         std::iota(idx.begin(), idx.end(), 0);
-        std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return np[x] > np[y]; });
+        std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+            const bool rx = !tiles || Ls[x] > kTileMaxL, ry = !tiles || Ls[y] > kTileMaxL;
+            if (rx != ry) return rx;
+            return np[x] > np[y];
+        });
+        pl.long_split = 0;
+        for (int64_t s = 0; s < nl; ++s) pl.long_split += (!tiles || Ls[s] > kTileMaxL) ? 1 : 0;
         pl.long_rows_h.resize(nl);
         pl.long_nprod_h.resize(nl);
         pl.long_L_h.resize(nl);
@@ -416,10 +434,10 @@ struct LongPlan {
     int32_t *ctr = nullptr;
 };
 
-// Long rows by column windows (brm_long_win.cuh): the plan's arrays, kept
-// from the pass that computes them (the symbolic pass of BRMerge-Precise and
-// of prepared batches; the numeric pass itself in BRMerge-Upper) to the
-// numeric pass, and the numeric kernel's per-warp scratch.
+// Long rows by column tiles (brm_long_win.cuh): the plan's arrays, kept from
+// the pass that computes them (the symbolic pass of BRMerge-Precise and of
+// prepared batches; the numeric pass itself in BRMerge-Upper) to the numeric
+// pass.  They cover the long slots [long_split, count).
 struct WinPlan {
     bool on = false;
     bool planned = false;          // a pass has launched the plan kernel
@@ -429,47 +447,37 @@ struct WinPlan {
     int64_t *rownnz = nullptr;
     int2 *spans = nullptr;
     unsigned long long *ctr = nullptr;
-    int4 *cur = nullptr;
-    void *hot = nullptr;
-    int32_t maxL = 0, grid = 0;
+    int32_t grid = 0;
 };
 
-// Whether the long rows of these passes take the column windows, and their
-// arrays: when the option is on, the bucket option off, B has at most 2^24
-// columns and every long row at most kWinMaxL lists.
+// The tiles' arrays, when the long rows of these passes take them.
 int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKind vnum, WinPlan &wp) {
     wp = WinPlan{};
-    const int64_t nl = (int64_t)pl.long_rows_h.size();
-    if (nl == 0 || !o.long_window || o.long_bucket || bcols > kLbMaxCols) return BRM_OK;
-    int64_t maxL = 0;
-    for (int64_t s = 0; s < nl; ++s) maxL = std::max<int64_t>(maxL, pl.long_L_h[s]);
-    if (maxL > kWinMaxL) return BRM_OK;
-    std::vector<int64_t> base((size_t)nl + 1, 0);
+    const int64_t nl = (int64_t)pl.long_rows_h.size(), s0 = pl.long_split;
+    if (nl == s0 || !tiles_apply(o, bcols)) return BRM_OK;
+    const int64_t nt = nl - s0;
+    std::vector<int64_t> base((size_t)nt + 1, 0);
     int64_t spans = 0;
-    for (int64_t s = 0; s < nl; ++s) {
-        base[s + 1] = base[s] + win_cap(pl.long_nprod_h[s], bcols);
-        spans += win_span_cap(pl.long_nprod_h[s]);
+    for (int64_t s = 0; s < nt; ++s) {
+        base[s + 1] = base[s] + win_cap(pl.long_nprod_h[s0 + s], bcols);
+        spans += win_span_cap(pl.long_nprod_h[s0 + s]);
     }
-    wp.maxL = (int32_t)std::max<int64_t>(maxL, 1);
     wp.grid = long_win_grid(vnum == kIdx ? kF64 : vnum);
-    const size_t warps = (size_t)wp.grid * kWinWarps;
     int rc;
-    if ((rc = get(mem, wp.base, (size_t)nl + 1, "window offsets"))) return rc;
-    if ((rc = get(mem, wp.rec, (size_t)std::max<int64_t>(base[nl], 1), "windows"))) return rc;
-    if ((rc = get(mem, wp.n, (size_t)nl, "window counts"))) return rc;
-    if ((rc = get(mem, wp.nws, (size_t)nl, "windows per span"))) return rc;
-    if ((rc = get(mem, wp.rownnz, (size_t)nl, "long-row lengths"))) return rc;
-    if ((rc = get(mem, wp.spans, (size_t)std::max<int64_t>(spans, 1), "window spans"))) return rc;
+    if ((rc = get(mem, wp.base, (size_t)nt + 1, "tile offsets"))) return rc;
+    if ((rc = get(mem, wp.rec, (size_t)std::max<int64_t>(base[nt], 1), "tiles"))) return rc;
+    if ((rc = get(mem, wp.n, (size_t)nt, "tile counts"))) return rc;
+    if ((rc = get(mem, wp.nws, (size_t)nt, "tiles per span"))) return rc;
+    if ((rc = get(mem, wp.rownnz, (size_t)nt, "long-row lengths"))) return rc;
+    if ((rc = get(mem, wp.spans, (size_t)std::max<int64_t>(spans, 1), "tile spans"))) return rc;
     if ((rc = get(mem, wp.ctr, 2, "span counters"))) return rc;
-    if ((rc = get(mem, wp.cur, warps * (size_t)wp.maxL, "list cursors"))) return rc;
-    if (!(wp.hot = mem.get(warps * kWinHotBytes))) return fail(BRM_ERR_OOM, "hot-window scratch");
     BRM_CUDA(cudaMemcpyAsync(wp.base, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
     wp.on = true;
     return BRM_OK;
 }
 
-// The window fields of a long-row job.
+// The tile fields of a long-row job.
 void win_job(RowJob &jb, const WinPlan &wp, bool plan_here) {
     jb.win = wp.rec;
     jb.win_base = wp.base;
@@ -478,18 +486,16 @@ void win_job(RowJob &jb, const WinPlan &wp, bool plan_here) {
     jb.win_rownnz = wp.rownnz;
     jb.win_spans = wp.spans;
     jb.win_ctr = wp.ctr;
-    jb.win_cur = wp.cur;
-    jb.win_hot = wp.hot;
-    jb.win_maxL = wp.maxL;
     jb.win_grid = wp.grid;
     jb.win_plan = plan_here ? 1 : 0;
 }
 
 int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp,
               bool persistent = true, const WinPlan *wp = nullptr) {
-    const int64_t nl = (int64_t)pl.long_rows_h.size();
+    // with column tiles, only the slots before long_split merge in rounds
+    const int64_t nl = (wp && wp->on) ? pl.long_split : (int64_t)pl.long_rows_h.size();
     lp.starts.clear();
-    if (nl == 0 || (wp && wp->on)) return BRM_OK;
+    if (nl == 0) return BRM_OK;
     // the symbolic pass counts long rows with the column bitmap whenever B has
     // at most 2^24 columns; the numeric pass uses column buckets on request
     // (they pack a list index into 16 bits and cut B's columns into at most
@@ -598,19 +604,17 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         PhaseScope ps(trace ? (v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg)) : -1, st);
         BRM_CUDA(launch_rows(v, b, jb, st));
     }
-    if (wp && wp->on) {
-        // every long row in one launch (two with the plan)
-        RowJob jb = j;
-        jb.rows = pl.long_rows_s;
-        jb.count = (int32_t)pl.long_rows_h.size();
-        jb.slot_nprod = pl.long_nprod_s;
-        win_job(jb, *wp, v == kIdx || !wp->planned);
-        PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
-        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
-        return BRM_OK;
-    }
-    if (lp.starts.size() < 2) return BRM_OK;
+    if (lp.starts.size() < 2 && !(wp && wp->on)) return BRM_OK;
     PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
+    if (wp && wp->on) {
+        // the tiled long rows in one launch (two with the plan)
+        RowJob jb = j;
+        jb.rows = pl.long_rows_s + pl.long_split;
+        jb.count = (int32_t)((int64_t)pl.long_rows_h.size() - pl.long_split);
+        jb.slot_nprod = pl.long_nprod_s + pl.long_split;
+        win_job(jb, *wp, v == kIdx || !wp->planned);
+        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
+    }
     for (size_t bi = 0; bi + 1 < lp.starts.size(); ++bi) {
         RowJob jb = j;
         jb.rows = pl.long_rows_s + lp.starts[bi];

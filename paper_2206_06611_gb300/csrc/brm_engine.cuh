@@ -218,11 +218,10 @@ struct RowJob {
     // from the counter (zero at launch), in the arena at arena_off[b]
     int32_t *long_ctr;
     int32_t long_grid;
-    // long rows by column windows (brm_long_win.cuh): per long slot, where its
-    // windows start (count + 1 entries), how many it has, windows per span,
-    // the row's distinct columns; the span list and its two counters (spans
-    // written, spans taken); per warp of the numeric kernel a cursor per list
-    // (win_maxL of them) and the state of a hot window
+    // long rows by column tiles (brm_long_win.cuh): per long slot, where its
+    // tiles start (count + 1 entries), how many it has, tiles per span, the
+    // row's distinct columns; the span list and its two counters (spans
+    // written, spans taken)
     struct WinRec *win;
     const int64_t *win_base;
     int32_t *win_n;
@@ -230,10 +229,7 @@ struct RowJob {
     int64_t *win_rownnz;
     int2 *win_spans;
     unsigned long long *win_ctr;
-    int4 *win_cur;
-    void *win_hot;
-    int32_t win_maxL;
-    int32_t win_grid;       // blocks of the numeric kernel (its scratch is sized for them)
+    int32_t win_grid;       // persistent blocks of the numeric kernel
     int32_t win_plan;       // 1: this pass computes the plan first (symbolic pass, or Upper)
 };
 

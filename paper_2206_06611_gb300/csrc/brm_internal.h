@@ -63,29 +63,27 @@ constexpr int kLbSlots = 65536;
 constexpr int kLbHotPerSm = 2;
 __host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUnit + 1) + 1; }
 
-// Long rows by column windows (brm_long_win.cuh): a window holds fewer than
-// kWinP products (one warp sorts them: 32 lanes x 32 keys) unless it is a
-// single cell of at most kWinCellMax columns; cuts every kWinH products;
-// at most kWinCells cells per bitmap window of kWinBitmapCols columns; rows
-// of at most kWinMaxL lists; spans of at least max(kWinSpanMin,
-// kWinSpanPerList * L) products; kWinWarps warps per block.
-constexpr int kWinP = 1024;
-constexpr int kWinH = kWinP / 2;
-constexpr int kWinPBits = 10;
+// Long rows by column tiles (brm_long_win.cuh): a tile holds at most kTileP
+// products (one thread block of kTileThreads sorts them) unless it is a single
+// cell of at most kWinCellMax columns (a "hot" tile, taken in chunks); the
+// plan cuts pieces every kWinH products and packs them into tiles; at most
+// kWinCells cells per bitmap window of kWinBitmapCols columns; rows of at most
+// kTileMaxL lists (longer ones keep the merge rounds); spans of at least
+// max(kWinSpanMin, kWinSpanPerList * L) products.
+constexpr int kTileP = 2048;
+constexpr int kTilePBits = 11;
+constexpr int kTileThreads = 256;
+constexpr int kTileMaxL = 2048;
+constexpr int kWinH = 256;
 constexpr int64_t kWinBitmapCols = (int64_t)1 << 20;
 constexpr int kWinCells = 8192;
 constexpr int kWinCellMax = (int)(kWinBitmapCols / kWinCells);
-constexpr int kWinMaxL = 65535;
 constexpr int64_t kWinSpanMin = 32768;
 constexpr int kWinSpanPerList = 16;
-constexpr int kWinWarps = 4;
-// per-warp scratch of the window kernel: for kWinCellMax columns an 8-byte
-// top sum, a level mask, the last list and 16 pending 8-byte sums; 16 closed
-// 8-byte sums per lane; rounded to 256
-constexpr size_t kWinHotBytes = ((size_t)((8 + 4 + 4 + 8 * 16) * kWinCellMax + 8 * 16 * 32) + 255) / 256 * 256;
-static_assert(kWinP == 32 * 32 && (1 << kWinPBits) == kWinP, "a window is sorted by one warp, 32 keys per lane");
+static_assert((1 << kTilePBits) == kTileP, "a tile position fits the key's low bits");
+static_assert(kTileMaxL <= kTileP, "one column of a tile holds at most kTileMaxL products");
 static_assert(kWinCellMax == 128, "cells are at most 128 columns wide");
-static_assert((kWinBitmapCols << kWinPBits) <= ((int64_t)1 << 32) - 1, "key = column offset and position");
+static_assert((kWinBitmapCols << kTilePBits) <= ((int64_t)1 << 32) - 1, "key = column offset and position");
 
 // One window of a long row: first column, products, and the number of the
 // row's distinct columns before it (its output offset inside the row).

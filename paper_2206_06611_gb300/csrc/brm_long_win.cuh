@@ -1,4 +1,4 @@
-// Long rows by column windows.
+// Long rows by column tiles.
 //
 // Algorithm 1 fixes the value at column c of a row as the sum of that column's
 // products A_it * B_tc over the lists t that hold c, added in the merge tree's
@@ -7,38 +7,52 @@
 // without c passing its partner's sum through.  Any procedure that adds each
 // column's products in that aligned binary tree gives Algorithm 1's bits,
 // whatever order the columns are visited in -- so a long row can be cut into
-// column ranges ("windows") that are merged independently, each by a warp,
-// instead of one thread block merging the whole row round by round.
+// column ranges ("tiles") that are reduced independently, each by one thread
+// block in shared memory, instead of one block merging the whole row round by
+// round through device memory.
 //
 // Plan (k_win_plan, one block per long row, index-only work):
 //   the row's columns are set in a shared-memory bitmap (one window of 2^20
 //   columns of B at a time) and its products counted per cell of 2^sh
 //   columns (at most 8192 cells per bitmap window, so a cell is at most 128
-//   columns wide).  Consecutive cells are grouped into windows: a cut
+//   columns wide).  Consecutive cells are grouped into pieces -- a cut
 //   wherever the running product count crosses a multiple of kWinH, and
-//   before and after every cell of more than kWinH products, so that a window
-//   holds fewer than 2 kWinH = kWinP products unless it is a single cell.
-//   Every window records its first column, its products and where its
-//   output starts inside the row (distinct columns before it).  The row's
-//   length (distinct columns) is the symbolic pass's result.  Consecutive
-//   windows are grouped into spans of at least max(32768, 16 L) products.
-// Numeric (k_long_win, persistent warps taking spans from a counter):
-//   a warp keeps one cursor per list of the row (the next position of B_t*
-//   not yet consumed, and its column), found by binary search at the span's
-//   first column.  For each window [c0, c1) in order it advances every cursor
-//   past c1: the elements passed form the list's segment in the window
-//   (empty for most lists of a wide row), segments in list order.  The
-//   window's products get positions p in segment order, hence in list order,
-//   and 32-bit keys ((column - c0) << 10) | p; the warp sorts them in
-//   registers (32 lanes x 32 keys, bitonic), and every run of equal columns
-//   -- its products in list order -- is reduced with a stack of partial sums
-//   whose separating levels bitlen(t_prev ^ t) strictly decrease.  Outputs go
-//   compacted to the window's known place in C.  A window of more than kWinP
-//   products (a single cell: at most 128 columns) is processed in chunks of
-//   kWinP products in list order; every column keeps its stack across the
-//   chunks (warp-private scratch in device memory) and is written at the end.
-// Limits: at most kWinMaxL lists per row (16-bit list index, stack depth),
-// B at most 2^24 columns; the host keeps the arena merge rounds otherwise.
+//   before and after every cell of more than kWinH products, so that a piece
+//   holds fewer than 2 kWinH products unless it is a single cell -- and the
+//   pieces are packed greedily into tiles of at most kTileP products (a
+//   piece of more is a single cell, and a tile of its own).  Every tile
+//   records its first column, its products and where its output starts
+//   inside the row (distinct columns before it).  The row's length (distinct
+//   columns) is the symbolic pass's result.  Consecutive tiles are grouped
+//   into spans of at least max(32768, 16 L) products.
+// Numeric (k_long_tile, persistent blocks taking spans from a counter):
+//   the block keeps one cursor per list of the row in shared memory (the
+//   next position of B_t* not yet consumed, its column, the list's end),
+//   found by binary search at the span's first column.  For a tile [c0, c1):
+//   1. every list's elements below c1 form its segment (a probe of the next
+//      four columns, for four lists at once, then a binary search bounded by
+//      c1 - column: B's columns are distinct), segments numbered in list
+//      order;
+//   2. the products are formed in that order -- position p in list order --
+//      with 32-bit keys ((column - c0) << 11) | p;
+//   3. a stable radix sort by column (8-bit digits, as many passes as the
+//      tile's columns need) puts every column's products together, still in
+//      list order;
+//   4. Algorithm 1's merge rounds run on the sorted positions: in round h
+//      every live sum takes the next live sum of its column when both have
+//      the same t >> h (left first), which is exactly what the rounds do to
+//      that column (a list without the column passes its partner through);
+//      every position is looked at by one thread, the rounds end when no
+//      sum can take a partner any more;
+//   5. the sums are written, compacted, at the tile's place in C.
+//   A hot tile (one cell of at most 128 columns with more than kTileP
+//   products) is taken in chunks of aligned list blocks [a 2^k, (a + 1) 2^k)
+//   of at most kTileP products: a chunk's sum at a column is the sum of a
+//   complete subtree of the merge tree, and the chunks' sums of every column
+//   are added by a tree stack per column, carried across the chunks, with
+//   the join level of two blocks bitlen(a1 2^k1 ^ a2 2^k2).
+// Limits: at most kTileMaxL lists per row (11-bit list levels), B at most
+// 2^24 columns; the host keeps the arena merge rounds for other long rows.
 #pragma once
 
 #include <algorithm>
@@ -56,12 +70,6 @@ namespace brm {
 static_assert(kLsWinBits == kWinBitmapCols, "the plan's bitmap window is the symbolic kernel's");
 static_assert(kWinCells % kLsThreads == 0, "plan: whole cells per thread");
 
-// Rows of at most this many lists keep their cursors in shared memory, longer
-// ones in the warp's slice of device memory.
-constexpr int kWinSmemL = 256;
-// Cursors loaded at once per lane (lists 32 apart).
-constexpr int kWinCurU = 4;
-
 // Cell shift for a bitmap window of wn columns: the smallest sh with
 // ceil(wn / 2^sh) <= kWinCells.
 __host__ __device__ constexpr int win_shift(int64_t wn) {
@@ -69,50 +77,17 @@ __host__ __device__ constexpr int win_shift(int64_t wn) {
     return b > 13 ? b - 13 : 0;
 }
 
-// Levels of the tree stack: two lists t1 < t2 < 65536 meet at level
-// bitlen(t1 ^ t2) in 1 .. 16.
-constexpr int kWinLevels = 16;
-constexpr uint32_t kWinEmpty = 0xffffffffu;   // carried state of a column that has no product yet
-
-// Per-warp scratch in device memory.  A window of more than kWinP products
-// (one cell, at most 128 columns) carries from chunk to chunk, for every
-// column, its tree stack (see WinStack): the top partial sum, the mask of
-// pending levels (kWinEmpty: no product yet), the last list added, and the
-// pending sums by level.  Then every lane's closed groups (see win_replay).
-template <class P>
-struct WinHot {
-    using T = typename P::T;
-    static constexpr size_t kTop = 0;                                       // T[128]
-    static constexpr size_t kMask = kTop + sizeof(T) * kWinCellMax;         // uint32[128]
-    static constexpr size_t kLast = kMask + 4 * kWinCellMax;                // int32[128]
-    static constexpr size_t kPend = kLast + 4 * kWinCellMax;                // T[kWinLevels][128]
-    static constexpr size_t kClosed = kPend + sizeof(T) * kWinLevels * kWinCellMax;   // T[32][kWinLevels]
-    static constexpr size_t kBytes = align_up(kClosed + sizeof(T) * 32 * kWinLevels, 256);
-    static_assert(kBytes <= kWinHotBytes, "per-warp hot-window scratch");
-};
-
-// Shared memory of one warp of the numeric kernel.  The segment tables are
-// read only by the gather; the sorted keys and the lanes' tree stacks
-// (two regions per lane: the run in progress, and the piece's first run when
-// it continues one from the lane before) are used only after it.
-template <class P>
-struct WinSmem {
-    using T = typename P::T;
-    static constexpr size_t kSegB = 0;                                      // int32[kWinP] B position - p
-    static constexpr size_t kSegT = kSegB + 4 * kWinP;                      // uint16[kWinP] list index
-    static constexpr size_t kBits = align_up(kSegT + 2 * kWinP, 16);        // uint32[32] segment starts
-    static constexpr size_t kWpre = kBits + 4 * 32;                         // int32[32] starts before a word
-    static constexpr size_t kGatherEnd = kWpre + 4 * 32;
-    static constexpr size_t kStage = 0;                                     // uint32[32 x 33] sorted keys
-    static constexpr size_t kPend = align_up(4 * 32 * 33, 16);              // T[2][32][kWinLevels]
-    static constexpr size_t kRunEnd = kPend + sizeof(T) * 2 * 32 * kWinLevels;
-    static constexpr size_t kVals = align_up(kGatherEnd > kRunEnd ? kGatherEnd : kRunEnd, 16);  // T[kWinP]
-    static constexpr size_t kLidx = kVals + sizeof(T) * kWinP;              // uint16[kWinP] list of position p
-    static constexpr size_t kHead = align_up(kLidx + 2 * kWinP, 16);        // T[32] top, then int4[32]
-    static constexpr size_t kHeadI = kHead + sizeof(T) * 32;                // int4: mask, g, closed | whole, last
-    static constexpr size_t kCur = align_up(kHeadI + 16 * 32, 16);          // int4[kWinSmemL] list cursors
-    static constexpr size_t kBytes = align_up(kCur + 16 * (size_t)kWinSmemL, 16);
-};
+// Levels of the tree: two lists t1 < t2 < kTileMaxL meet at level
+// bitlen(t1 ^ t2) in 1 .. 11.
+constexpr int kTileLevels = 11;
+static_assert((1 << kTileLevels) == kTileMaxL, "list levels");
+constexpr uint32_t kWinEmpty = 0xffffffffu;   // carried state of a column that has no sum yet
+constexpr uint32_t kTilePMask = (1u << kTilePBits) - 1u;
+constexpr uint16_t kTileRet = 0x8000u;         // a retired position of the merge rounds
+static_assert(kTileP < kTileRet, "positions fit 15 bits");
+constexpr int kTileNW = kTileThreads / 32;
+constexpr int kTileQ = kTileP / kTileThreads;   // sorted positions per thread
+static_assert(kTileThreads == 256, "one radix digit per thread");
 
 // ---------------------------------------------------------------------------
 // Plan
@@ -125,6 +100,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
     __shared__ int32_t s_off[kLsThreads + 1];
     __shared__ int ws[kLsThreads / 32 + 1];
     __shared__ int64_t s_span[2];
+    __shared__ int64_t s_nwin;
     constexpr int NT = kLsThreads, PER = kWinCells / NT, K = 8;
     BlockGrp<NT> g;
     g.ws = ws;
@@ -243,19 +219,30 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                 Dc[nc] = totd;
             }
             g.sync();
-            if (nwin + ftot <= cap) {
-                for (int q = tid; q < ftot; q += NT) {
-                    const int d0 = ul[q], d1 = ul[q + 1];
-                    WinRec rec;
-                    rec.c0 = (int32_t)(w0 + ((int64_t)d0 << sh));
-                    rec.np = Sc[d1] - Sc[d0];
-                    rec.off = count + Dc[d0];
-                    wr[nwin + q] = rec;
+            // tiles: consecutive pieces packed greedily up to kTileP products
+            // (a piece of more is one cell and a tile of its own)
+            if (tid == 0) {
+                int64_t nw = nwin;
+                for (int q = 0; q < ftot;) {
+                    const int d0 = ul[q];
+                    int q1 = q + 1;
+                    while (q1 < ftot && Sc[ul[q1 + 1]] - Sc[d0] <= kTileP) ++q1;
+                    if (nw < cap) {
+                        WinRec rec;
+                        rec.c0 = (int32_t)(w0 + ((int64_t)d0 << sh));
+                        rec.np = Sc[ul[q1]] - Sc[d0];
+                        rec.off = count + Dc[d0];
+                        wr[nw] = rec;
+                    } else if (j.err != nullptr) {
+                        atomicOr(j.err, 2u);   // cannot happen: the capacity bounds the pieces
+                    }
+                    ++nw;
+                    q = q1;
                 }
-            } else if (tid == 0 && j.err != nullptr) {
-                atomicOr(j.err, 2u);   // cannot happen: the capacity bounds the cuts
+                s_nwin = min(nw, cap);
             }
-            nwin = min(nwin + ftot, cap);
+            g.sync();
+            nwin = s_nwin;
             count += totd;
             prod += totp;
             g.sync();   // the cut list is read before the bitmap is cleared again
@@ -291,16 +278,17 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
 // Numeric pass
 // ---------------------------------------------------------------------------
 
-// Tree stack of one column's products in list order, by level.  The products
-// added so far (lists up to `last`) form partial sums waiting for their
-// right neighbours: pend[h] is the one that meets the sums after it at level
-// h (bit h of mask), top the most recent one.  The pending levels strictly
-// decrease from the oldest sum to the newest, so the mask determines the
-// order.  Adding a product (or a finished group of them) whose join level
-// with the previous one is d first completes every sum below level d --
-// lowest level first, the older (left) sum first -- then parks the result at
-// level d.  This performs the additions of Algorithm 1's merge rounds for
-// the column in their order.  Pending sums live in memory with a stride.
+// Tree stack of one column's sums in list order, by level.  The sums added so
+// far (lists up to `last`) form partial sums waiting for their right
+// neighbours: pend[h] is the one that meets the sums after it at level h (bit
+// h of mask), top the most recent one.  The pending levels strictly decrease
+// from the oldest sum to the newest, so the mask determines the order.
+// Adding a product (or the finished sum of a complete subtree) whose join
+// level with the previous one is d first completes every sum below level d
+// -- lowest level first, the older (left) sum first -- then parks the result
+// at level d.  This performs the additions of Algorithm 1's merge rounds for
+// the column in their order.  Pending sums live in memory with a stride
+// (the carried stacks of a hot tile's columns).
 template <class P, class Ptr>
 struct WinStack {
     using T = typename P::T;
@@ -311,7 +299,7 @@ struct WinStack {
     int last;
 
     __device__ __forceinline__ void push(T v, int d) {
-        d = d < 1 ? 1 : (d > kWinLevels ? kWinLevels : d);   // out of range only for invalid input
+        d = d < 1 ? 1 : (d > kTileLevels ? kTileLevels : d);   // out of range only for invalid input
         const uint32_t below = (1u << d) - 1u;
         uint32_t m = mask & below;
         while (m) {
@@ -336,326 +324,411 @@ struct WinStack {
     }
 };
 
-// A lane's piece that continues a run from the lane before it cannot add its
-// products to the sums before it, but knows the level g at which its first
-// product meets the run's previous one.  While the levels it sees stay below
-// g it is an ordinary tree stack; when a product arrives whose level d is
-// above g, the whole stack would join the sums before it first, so it is
-// finished and set aside as a closed group at level g, and the product starts
-// a new stack at level d.  The lane that owns the run appends the closed
-// groups (at their levels, lowest first) and then the open stack, oldest sum
-// first, which repeats the additions of one tree stack fed product by
-// product.
-template <class P, class PtrA>
-__device__ __forceinline__ void win_replay(WinStack<P, PtrA> &acc, const typename P::T *closed, uint32_t cmask,
-                                           const typename P::T *pend, uint32_t mask, int g, typename P::T top,
-                                           int last) {
-    while (cmask) {
-        const int h = __ffs(cmask) - 1;
-        acc.push(closed[h - 1], h);
-        cmask &= cmask - 1u;
-    }
-    int d = g;
-    while (mask) {
-        const int h = 31 - __clz(mask);
-        acc.push(pend[h - 1], d);
-        d = h;
-        mask &= ~(1u << h);
-    }
-    acc.push(top, d);
-    acc.last = last;
-}
+__device__ __forceinline__ int tile_bitlen(uint32_t x) { return 32 - __clz((int)x); }
 
-// Segment (index) of window position p: the starts up to p, minus one.
-__device__ __forceinline__ int win_seg(const uint32_t *bits, const int32_t *wpre, int p) {
-    const uint32_t m = bits[p >> 5] & (0xffffffffu >> (31 - (p & 31)));
-    return wpre[p >> 5] + __popc(m) - 1;
-}
-
-// What the chunk step of a window needs.
+// Shared memory of the numeric kernel (one block).  The per-list scratch of
+// the segment search (lengths and first positions) borrows the key buffers,
+// which the products fill only after it; the merge rounds' links borrow the
+// key buffer that does not hold the sorted keys.
 template <class P>
-struct WinCtx {
-    unsigned char *wb;       // the warp's shared memory (WinSmem layout)
-    unsigned char *hs;       // the warp's hot-window scratch
-    typename P::T *closed;   // the warp's closed groups: 32 lanes x kWinLevels
-    const typename P::In *aval;
-    const int32_t *bcol;
-    const typename P::In *bval;
-    uint64_t keep;
-    int c0;
-    bool hot;
-    int32_t *ocol;           // the window's first output
-    typename P::Out *oval;
-    int64_t expect;          // the window's distinct columns
+struct TileSmem {
+    using T = typename P::T;
+    static constexpr size_t kCpos = 0;                                              // int32[kTileMaxL]
+    static constexpr size_t kCcol = kCpos + 4 * kTileMaxL;                          // int32[kTileMaxL]
+    static constexpr size_t kCend = kCcol + 4 * kTileMaxL;                          // int32[kTileMaxL]
+    static constexpr size_t kSegQ = kCend + 4 * kTileMaxL;                          // int32[kTileMaxL]
+    static constexpr size_t kSegOff = kSegQ + 4 * kTileMaxL;                        // int32[kTileMaxL + 1]
+    static constexpr size_t kSegT = align_up(kSegOff + 4 * (kTileMaxL + 1), 16);    // uint16[kTileMaxL]
+    static constexpr size_t kBits = align_up(kSegT + 2 * kTileMaxL, 16);            // uint32[kTileP / 32]
+    static constexpr size_t kWpre = kBits + 4 * (kTileP / 32);                      // int32[kTileP / 32]
+    static constexpr size_t kKeyA = kWpre + 4 * (kTileP / 32);                      // uint32[kTileP]
+    static constexpr size_t kKeyB = kKeyA + 4 * kTileP;                             // uint32[kTileP]
+    static constexpr size_t kVals = kKeyB + 4 * kTileP;                             // T[kTileP]
+    static constexpr size_t kLidx = kVals + sizeof(T) * kTileP;                     // uint16[kTileP]
+    static constexpr size_t kCnt = align_up(kLidx + 2 * kTileP, 16);                // uint16[kTileNW][256]
+    static constexpr size_t kHTop = align_up(kCnt + 2 * kTileNW * 256, 16);         // T[kWinCellMax]
+    static constexpr size_t kHPend = kHTop + sizeof(T) * kWinCellMax;               // T[kTileLevels][kWinCellMax]
+    static constexpr size_t kHMask = kHPend + sizeof(T) * kTileLevels * kWinCellMax;   // uint32[kWinCellMax]
+    static constexpr size_t kHLast = kHMask + 4 * kWinCellMax;                      // int32[kWinCellMax]
+    static constexpr size_t kBytes = align_up(kHLast + 4 * kWinCellMax, 16);
+    static_assert(kTileP >= kTileMaxL, "the search scratch fits a key buffer");
 };
 
-// A finished run of column c0 + cr: written at output wpos (a window that
-// fits one sort), or stored as the column's carried stack (a hot window).
-template <class P, class Ptr>
-__device__ __forceinline__ void win_emit(const WinCtx<P> &x, uint32_t cr, int64_t wpos, const WinStack<P, Ptr> &st) {
-    using T = typename P::T;
-    using H = WinHot<P>;
-    if (!x.hot) {
-        if (wpos < x.expect) {
-            __stcs(x.ocol + wpos, (int32_t)(x.c0 + (int)cr));
-            __stcs(x.oval + wpos, P::fin(st.finish()));
-        }
-        return;
-    }
-    T *gpend = reinterpret_cast<T *>(x.hs + H::kPend) + cr;
-    uint32_t m = st.mask;
-    while (m) {
-        const int h = __ffs(m) - 1;
-        gpend[(h - 1) * kWinCellMax] = st.pend[(h - 1) * st.stride];
-        m &= m - 1u;
-    }
-    reinterpret_cast<T *>(x.hs + H::kTop)[cr] = st.top;
-    reinterpret_cast<uint32_t *>(x.hs + H::kMask)[cr] = st.mask;
-    reinterpret_cast<int32_t *>(x.hs + H::kLast)[cr] = st.last;
-}
-
-// One chunk of n products of a window (positions 0 .. n-1 in list order,
-// segments recorded in the gather tables): gather the products, sort the
-// keys ((column - c0) << 10 | p) in registers, then reduce the runs of equal
-// columns.  Lane l reduces sorted positions 32 l .. 32 l + 31 with its tree
-// stack; a run that continues into later lanes is finished by the lane where
-// it starts, which appends the later lanes' stacks in order.  Returns the
-// outputs written (a window that fits one sort).
-template <class P>
-__device__ __noinline__ int win_chunk(const WinCtx<P> &x, int n, int64_t count) {
-    using In = typename P::In;
-    using T = typename P::T;
-    using S = WinSmem<P>;
-    constexpr unsigned kFull = 0xffffffffu;
-    constexpr uint32_t PM = (1u << kWinPBits) - 1u;
-    const int lane = threadIdx.x & 31;
-    int32_t *segb = reinterpret_cast<int32_t *>(x.wb + S::kSegB);
-    uint16_t *segt = reinterpret_cast<uint16_t *>(x.wb + S::kSegT);
-    uint32_t *bits = reinterpret_cast<uint32_t *>(x.wb + S::kBits);
-    int32_t *wpre = reinterpret_cast<int32_t *>(x.wb + S::kWpre);
-    uint32_t *stage = reinterpret_cast<uint32_t *>(x.wb + S::kStage);
-    T *pendb = reinterpret_cast<T *>(x.wb + S::kPend);
-    T *vals = reinterpret_cast<T *>(x.wb + S::kVals);
-    uint16_t *lidx = reinterpret_cast<uint16_t *>(x.wb + S::kLidx);
-    T *htop = reinterpret_cast<T *>(x.wb + S::kHead);
-    int4 *hinfo = reinterpret_cast<int4 *>(x.wb + S::kHeadI);
-    // segment starts before every word of the start bitmap
-    {
-        const int c = __popc(bits[lane]);
-        int v = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(kFull, v, d);
-            if (lane >= d) v += y;
-        }
-        wpre[lane] = v - c;
-    }
-    __syncwarp();
-    uint32_t key[32];
-#pragma unroll
-    for (int i0 = 0; i0 < 32; i0 += kRegU) {
-        int q[kRegU], t[kRegU];
-        In a[kRegU];
-#pragma unroll
-        for (int u = 0; u < kRegU; ++u) {
-            const int p = (i0 + u) * 32 + lane;
-            q[u] = -1;
-            t[u] = 0;
-            a[u] = In();
-            if (p < n) {
-                const int sg = win_seg(bits, wpre, p);
-                q[u] = segb[sg] + p;
-                t[u] = segt[sg];
-                a[u] = __ldg(x.aval + t[u]);
-            }
-        }
-        int32_t c[kRegU];
-        In v[kRegU];
-#pragma unroll
-        for (int u = 0; u < kRegU; ++u) {
-            c[u] = 0;
-            v[u] = In();
-            if (q[u] >= 0) {
-                c[u] = ld_keep(x.bcol + q[u], x.keep);
-                v[u] = ld_keep(x.bval + q[u], x.keep);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kRegU; ++u) {
-            const int p = (i0 + u) * 32 + lane;
-            key[i0 + u] = kKeyPad;
-            if (q[u] >= 0) {
-                key[i0 + u] = ((uint32_t)(c[u] - x.c0) << kWinPBits) | (uint32_t)p;
-                vals[p] = P::mul(a[u], v[u]);
-                lidx[p] = (uint16_t)t[u];
-            }
-        }
-    }
-    reg_bitonic_sort<32, 32>(key, lane);
-    __syncwarp();   // every lane's gather has read the tables the key tile overwrites
-    // lane l holds sorted positions 32 l + i in key[i]; run starts and the
-    // runs that cross from one lane into the next
-    const uint32_t prv = __shfl_up_sync(kFull, key[31], 1);
-    const uint32_t nxt = __shfl_down_sync(kFull, key[0], 1);
-    const bool cont_in = lane > 0 && key[0] != kKeyPad && (prv >> kWinPBits) == (key[0] >> kWinPBits);
-    const bool cont_out = lane < 31 && key[31] != kKeyPad && nxt != kKeyPad &&
-                          (nxt >> kWinPBits) == (key[31] >> kWinPBits);
-    int nst = 0;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        stage[i * 33 + lane] = key[i];
-        const bool real = key[i] != kKeyPad;
-        const bool start = real && (i == 0 ? !cont_in : (key[i] >> kWinPBits) != (key[i - 1] >> kWinPBits));
-        nst += start ? 1 : 0;
-    }
-    int base = nst;
+// Exclusive prefix sums of (a, b) over the block, totals in (ta, tb).
+__device__ __forceinline__ int2 tile_scan2(int a, int b, int &ta, int &tb, int2 *ws) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = a, y = b;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(kFull, base, d);
-        if (lane >= d) base += y;
-    }
-    const int total = __shfl_sync(kFull, base, 31);
-    base = base - nst;
-    __syncwarp();
-
-    // this lane's piece, position by position: runs that start here are
-    // reduced in pendR (a hot window's continuing from the column's carried
-    // stack); a first run that continues one from the lane before, in pendH
-    // with closed groups (see win_replay)
-    using H = WinHot<P>;
-    T *pendR = pendb + lane * kWinLevels, *pendH = pendb + (32 + lane) * kWinLevels;
-    T *closedL = x.closed + lane * kWinLevels;
-    int g0 = 0;
-    if (cont_in) g0 = 32 - __clz((int)lidx[prv & PM] ^ (int)lidx[key[0] & PM]);
-    WinStack<P, T *> st{pendR, 1, T(), 0u, 0};
-    uint32_t cc = kKeyPad;   // column of the run in progress
-    int done = 0, g = 0;
-    uint32_t cmask = 0;
-    bool head = false;
-    for (int i = 0; i < 32; ++i) {
-        const uint32_t k = stage[i * 33 + lane];
-        if (k == kKeyPad) break;
-        const uint32_t c = k >> kWinPBits;
-        const int p = (int)(k & PM);
-        const T v = vals[p];
-        const int t = lidx[p];
-        if (c != cc) {
-            if (cc != kKeyPad) {
-                if (head) {
-                    htop[lane] = st.top;
-                    hinfo[lane] = make_int4((int)st.mask, g, (int)cmask, st.last);
-                } else {
-                    win_emit<P>(x, cc, count + base + done, st);
-                    ++done;
-                }
-            }
-            head = i == 0 && cont_in;
-            cc = c;
-            if (head) {
-                st.pend = pendH;
-                st.top = v;
-                st.mask = 0u;
-                st.last = t;
-                g = g0;
-                cmask = 0u;
-            } else {
-                st.pend = pendR;
-                const uint32_t gm = x.hot ? reinterpret_cast<const uint32_t *>(x.hs + H::kMask)[c] : kWinEmpty;
-                if (gm != kWinEmpty) {
-                    // the column's stack from the chunks before
-                    const T *gpend = reinterpret_cast<const T *>(x.hs + H::kPend) + c;
-                    uint32_t m = gm;
-                    while (m) {
-                        const int h = __ffs(m) - 1;
-                        pendR[h - 1] = gpend[(h - 1) * kWinCellMax];
-                        m &= m - 1u;
-                    }
-                    st.top = reinterpret_cast<const T *>(x.hs + H::kTop)[c];
-                    st.mask = gm;
-                    st.last = reinterpret_cast<const int32_t *>(x.hs + H::kLast)[c];
-                    st.push(v, 32 - __clz(st.last ^ t));
-                    st.last = t;
-                } else {
-                    st.top = v;
-                    st.mask = 0u;
-                    st.last = t;
-                }
-            }
-        } else if (head) {
-            const int d = 32 - __clz(st.last ^ t);
-            if (d < g) {
-                st.push(v, d);
-            } else {
-                closedL[g - 1] = st.finish();
-                cmask |= 1u << g;
-                st.top = v;
-                st.mask = 0u;
-                g = d;
-            }
-            st.last = t;
-        } else {
-            st.push(v, 32 - __clz(st.last ^ t));
-            st.last = t;
+        const int ux = __shfl_up_sync(0xffffffffu, x, d);
+        const int uy = __shfl_up_sync(0xffffffffu, y, d);
+        if (lane >= d) {
+            x += ux;
+            y += uy;
         }
     }
-    // the last run of the piece: finished here, or continued by the next lanes
-    bool own_tail = false;
-    if (cc != kKeyPad) {
-        if (head) {
-            htop[lane] = st.top;
-            hinfo[lane] = make_int4((int)st.mask, g, (int)(cmask | (cont_out ? 0x80000000u : 0u)), st.last);
-        } else if (cont_out) {
-            own_tail = true;
-        } else {
-            win_emit<P>(x, cc, count + base + done, st);
-            ++done;
+    if (lane == 31) ws[wid] = make_int2(x, y);
+    __syncthreads();
+    if (wid == 0) {
+        int2 w = lane < kTileNW ? ws[lane] : make_int2(0, 0);
+        const int2 w0 = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int ux = __shfl_up_sync(0xffffffffu, w.x, d);
+            const int uy = __shfl_up_sync(0xffffffffu, w.y, d);
+            if (lane >= d) {
+                w.x += ux;
+                w.y += uy;
+            }
         }
+        if (lane < kTileNW) ws[lane] = make_int2(w.x - w0.x, w.y - w0.y);
+        if (lane == kTileNW - 1) ws[kTileNW] = w;
     }
-    __syncwarp();   // every lane's first-run stack is published
-    if (own_tail) {
-        for (int l = lane + 1; l < 32; ++l) {
-            const int4 hi = hinfo[l];
-            const uint32_t cm = (uint32_t)hi.z;
-            win_replay<P>(st, x.closed + l * kWinLevels, cm & 0x7fffffffu, pendb + (32 + l) * kWinLevels,
-                          (uint32_t)hi.x, hi.y, htop[l], hi.w);
-            if (!(cm >> 31)) break;
-        }
-        win_emit<P>(x, cc, count + base + done, st);
-        ++done;
-    }
-    __syncwarp();   // the chunk's buffers are refilled next
-    bits[lane] = 0u;
-    __syncwarp();
-    return x.hot ? 0 : total;
+    __syncthreads();
+    const int2 r = make_int2(ws[wid].x + x - a, ws[wid].y + y - b);
+    ta = ws[kTileNW].x;
+    tb = ws[kTileNW].y;
+    __syncthreads();   // ws may be reused right away
+    return r;
 }
 
+// One pass of a stable radix sort of n <= kTileP keys by the 8-bit digit at
+// `shift`: warp w ranks keys [w * kTileQ * 32, (w + 1) * kTileQ * 32) in
+// order (lanes with equal digits found by __match_any_sync), the digit
+// offsets are laid out digit-major and warp-minor, and every key moves to
+// its digit's offset plus its rank.
+__device__ __forceinline__ void tile_radix_pass(const uint32_t *src, uint32_t *dst, int n, int shift, uint16_t *cnt,
+                                                int *ws) {
+    BlockGrp<kTileThreads> g;
+    g.ws = ws;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < kTileNW * 256; i += kTileThreads) cnt[i] = 0;
+    __syncthreads();
+    uint16_t *wc = cnt + w * 256;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t key[kTileQ];
+    int rk[kTileQ];
+#pragma unroll
+    for (int it = 0; it < kTileQ; ++it) {
+        const int idx = w * (32 * kTileQ) + it * 32 + lane;
+        const bool ok = idx < n;
+        key[it] = ok ? src[idx] : 0u;
+        const int d = ok ? (int)((key[it] >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int before = ok ? (int)wc[d] : 0;
+        rk[it] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wc[d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // thread tid lays out digit tid
+        int c[kTileNW], tot = 0;
+#pragma unroll
+        for (int v = 0; v < kTileNW; ++v) {
+            c[v] = cnt[v * 256 + tid];
+            tot += c[v];
+        }
+        int all;
+        int base = g.scan_excl(tot, all);
+#pragma unroll
+        for (int v = 0; v < kTileNW; ++v) {
+            cnt[v * 256 + tid] = (uint16_t)base;
+            base += c[v];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kTileQ; ++it) {
+        const int idx = w * (32 * kTileQ) + it * 32 + lane;
+        if (idx < n) dst[(int)wc[(key[it] >> shift) & 255u] + rk[it]] = key[it];
+    }
+    __syncthreads();
+}
+
+// What the chunk step of a tile needs (shared memory, the row, the tile).
 template <class P>
-__global__ void __launch_bounds__(kWinWarps * 32) k_long_win(RowJob j) {
+struct TileCtx {
     using In = typename P::In;
     using T = typename P::T;
     using Out = typename P::Out;
-    using S = WinSmem<P>;
-    using H = WinHot<P>;
+    const int32_t *segq, *segoff;
+    const uint16_t *segt;
+    uint32_t *bits;
+    int32_t *wpre;
+    uint32_t *keyA, *keyB;
+    T *vals;
+    uint16_t *lidx;
+    uint16_t *cnt;
+    T *htop, *hpend;
+    uint32_t *hmask;
+    int32_t *hlast;
+    int *s_int;            // [0] largest column offset
+    int *ws;               // block scan scratch
+    const In *aval;
+    const int32_t *bcol;
+    const In *bval;
+    uint64_t keep;
+    int c0;
+    int32_t *ocol;         // the tile's first output
+    Out *oval;
+    int64_t expect;        // the tile's distinct columns
+    unsigned int *err;
+};
+
+// A finished sum of column c0 + col: written at the tile's output ridx, or --
+// in a hot tile's chunk, whose sum is that of the aligned list block starting
+// at tb -- added to the column's carried stack.
+template <class P>
+__device__ __forceinline__ void tile_emit(const TileCtx<P> &x, bool hot, int tb, int ridx, uint32_t col,
+                                          typename P::T v) {
+    using T = typename P::T;
+    if (!hot) {
+        if (ridx < x.expect) {
+            __stcs(x.ocol + ridx, (int32_t)(x.c0 + (int)col));
+            __stcs(x.oval + ridx, P::fin(v));
+        }
+        return;
+    }
+    if (col >= (uint32_t)kWinCellMax) {
+        atomicOr(x.err, 2u);   // cannot happen: a hot tile is one cell
+        return;
+    }
+    const uint32_t hm = x.hmask[col];
+    if (hm == kWinEmpty) {
+        x.htop[col] = v;
+        x.hmask[col] = 0u;
+    } else {
+        WinStack<P, T *> st{x.hpend + col, kWinCellMax, x.htop[col], hm, 0};
+        st.push(v, tile_bitlen((uint32_t)(x.hlast[col] ^ tb)));
+        x.htop[col] = st.top;
+        x.hmask[col] = st.mask;
+    }
+    x.hlast[col] = tb;
+}
+
+// One chunk of a tile: the products of segments [sa, sb), tile positions
+// [pos0, pos0 + n), 0 < n <= kTileP: gather in list order, sort by column,
+// add every column's products in tree order, emit.  Called by every thread of
+// the block; returns the columns of the chunk.
+template <class P>
+__device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, bool hot, int tb) {
+    using In = typename P::In;
     constexpr unsigned kFull = 0xffffffffu;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char *wb = smem + (size_t)wid * S::kBytes;
-    int32_t *segb = reinterpret_cast<int32_t *>(wb + S::kSegB);
-    uint16_t *segt = reinterpret_cast<uint16_t *>(wb + S::kSegT);
-    uint32_t *bits = reinterpret_cast<uint32_t *>(wb + S::kBits);
-    const int64_t gw = (int64_t)blockIdx.x * kWinWarps + wid;
-    int4 *cur_g = j.win_cur + gw * (int64_t)j.win_maxL;
-    int4 *cur_s = reinterpret_cast<int4 *>(wb + S::kCur);
-    unsigned char *hs = reinterpret_cast<unsigned char *>(j.win_hot) + gw * (int64_t)H::kBytes;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // 1. segment starts of the chunk, and the starts before every word
+    const int nw = (n + 31) >> 5;
+    for (int i = tid; i < nw; i += kTileThreads) x.bits[i] = 0u;
+    if (tid == 0) x.s_int[0] = 0;
+    __syncthreads();
+    for (int s = sa + tid; s < sb; s += kTileThreads) {
+        const int st = max(x.segoff[s], pos0) - pos0;
+        atomicOr(&x.bits[st >> 5], 1u << (st & 31));
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int i0 = 2 * lane, i1 = 2 * lane + 1;
+        const int p0 = i0 < nw ? __popc(x.bits[i0]) : 0, p1 = i1 < nw ? __popc(x.bits[i1]) : 0;
+        int v = p0 + p1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(kFull, v, d);
+            if (lane >= d) v += u;
+        }
+        const int ex = v - p0 - p1;
+        if (i0 < nw) x.wpre[i0] = ex;
+        if (i1 < nw) x.wpre[i1] = ex + p0;
+    }
+    __syncthreads();
+    // 2. the products in list order: key ((column - c0) << 11) | position
+    {
+        int q[kTileQ], t[kTileQ];
+#pragma unroll
+        for (int i = 0; i < kTileQ; ++i) {
+            const int p = tid + kTileThreads * i;
+            q[i] = -1;
+            t[i] = 0;
+            if (p < n) {
+                const int w = p >> 5;
+                const int sg = sa + x.wpre[w] + __popc(x.bits[w] & (kFull >> (31 - (p & 31)))) - 1;
+                q[i] = x.segq[sg] + (pos0 + p - x.segoff[sg]);
+                t[i] = x.segt[sg];
+            }
+        }
+        int32_t c[kTileQ];
+        In v[kTileQ], a[kTileQ];
+#pragma unroll
+        for (int i = 0; i < kTileQ; ++i) {
+            c[i] = 0;
+            v[i] = In();
+            a[i] = In();
+            if (q[i] >= 0) {
+                c[i] = ld_keep(x.bcol + q[i], x.keep);
+                v[i] = ld_keep(x.bval + q[i], x.keep);
+                a[i] = __ldg(x.aval + t[i]);
+            }
+        }
+        uint32_t mx = 0;
+#pragma unroll
+        for (int i = 0; i < kTileQ; ++i) {
+            const int p = tid + kTileThreads * i;
+            if (q[i] >= 0) {
+                uint32_t co = (uint32_t)(c[i] - x.c0);
+                if (co >= (uint32_t)kWinBitmapCols) {
+                    atomicOr(x.err, 2u);   // cannot happen: a tile lies inside one bitmap window
+                    co = (uint32_t)kWinBitmapCols - 1u;
+                }
+                x.keyA[p] = (co << kTilePBits) | (uint32_t)p;
+                x.vals[p] = P::mul(a[i], v[i]);
+                x.lidx[p] = (uint16_t)t[i];
+                mx = max(mx, co);
+            }
+        }
+        mx = __reduce_max_sync(kFull, mx);
+        if (lane == 0 && mx) atomicMax(reinterpret_cast<unsigned int *>(&x.s_int[0]), mx);
+    }
+    __syncthreads();
+    // 3. stable sort by column: the positions of equal columns stay in list order
+    const uint32_t maxco = (uint32_t)x.s_int[0];
+    const int cbits = maxco ? tile_bitlen(maxco) : 0;
+    uint32_t *src = x.keyA, *dst = x.keyB;
+    for (int sh = 0; sh < cbits; sh += 8) {
+        tile_radix_pass(src, dst, n, kTilePBits + sh, x.cnt, x.ws);
+        uint32_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    const uint32_t *K = src;
+    // 4. Algorithm 1's merge rounds on the sorted positions.  Within a column
+    // the positions are in list order; after round h - 1 the live sums of a
+    // column have distinct t >> (h - 1), t the smallest list of the sum.
+    // Round h adds to every live sum the next live sum of its column when
+    // both have the same t >> h (the left one first) and retires the right
+    // one.  Two sums that meet in round h are neighbours among the live sums
+    // of their column: a retired position is never read again, and a sum
+    // that takes a partner is never taken in the same round (three live sums
+    // of one column cannot share t >> h).  The leftmost sum of a column is
+    // never retired: it ends as the column's value.
+    uint16_t *nxt = reinterpret_cast<uint16_t *>(dst);           // next live position (kTileRet: retired)
+    uint16_t *st = nxt + kTileP;                                  // smallest list of the sum at a position
+    BlockGrp<kTileThreads> g;
+    g.ws = x.ws;
+    const int s0 = tid * kTileQ;
+    uint32_t stm = 0, live = 0;
+#pragma unroll
+    for (int i = 0; i < kTileQ; ++i) {
+        const int s = s0 + i;
+        if (s < n) {
+            const uint32_t k = K[s];
+            st[s] = x.lidx[k & kTilePMask];
+            nxt[s] = (uint16_t)(s + 1);
+            live |= 1u << i;
+            if (s == 0 || (K[s - 1] >> kTilePBits) != (k >> kTilePBits)) stm |= 1u << i;
+        }
+    }
+    int nruns;
+    const int rbase = g.scan_excl(__popc(stm), nruns);   // its barriers publish nxt and st
+    const int hmax = tile_bitlen((uint32_t)(x.segt[sa] ^ x.segt[sb - 1]));
+    for (int h = 1; h <= hmax; ++h) {
+        uint32_t m = live;
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            const int s = s0 + i;
+            const int j = nxt[s];
+            const uint32_t ks = K[s];
+            if ((j & kTileRet) || j >= n || (K[j] >> kTilePBits) != (ks >> kTilePBits)) {
+                // retired, or the last live sum of its column: no partner ever
+                live &= ~(1u << i);
+                continue;
+            }
+            if ((st[s] >> h) != (st[j] >> h)) continue;
+            const int ps = (int)(ks & kTilePMask), pj = (int)(K[j] & kTilePMask);
+            x.vals[ps] = P::add(x.vals[ps], x.vals[pj]);
+            nxt[s] = nxt[j];
+            nxt[j] = (uint16_t)(nxt[j] | kTileRet);
+        }
+        if (!__syncthreads_or(live != 0u)) break;
+    }
+    __syncthreads();
+    // 5. the columns' values
+    int ridx = rbase;
+    while (stm) {
+        const int i = __ffs(stm) - 1;
+        stm &= stm - 1u;
+        const uint32_t k = K[s0 + i];
+        tile_emit<P>(x, hot, tb, ridx, k >> kTilePBits, x.vals[k & kTilePMask]);
+        ++ridx;
+    }
+    __syncthreads();   // the chunk's buffers are refilled next
+    return nruns;
+}
+
+// First position of B_t*[pos + 1 .. hi) whose column is c1 or more (hi if
+// none), by binary search.
+__device__ __forceinline__ int tile_seg_end(const int32_t *bcol, int pos, int hi, int c1) {
+    int lo = pos + 1, h = hi;
+    while (lo < h) {
+        const int mid = (lo + h) >> 1;
+        if (__ldg(bcol + mid) < c1) lo = mid + 1; else h = mid;
+    }
+    return lo;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
+    using In = typename P::In;
+    using T = typename P::T;
+    using Out = typename P::Out;
+    using S = TileSmem<P>;
+    constexpr int NT = kTileThreads;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int ws[kTileNW + 1];
+    __shared__ int2 ws2[kTileNW + 1];
+    __shared__ int s_int[1];
+    __shared__ int s_chunk[4];
+    __shared__ unsigned long long s_span;
+    const int tid = threadIdx.x;
+    int32_t *cpos = reinterpret_cast<int32_t *>(sm + S::kCpos);
+    int32_t *ccol = reinterpret_cast<int32_t *>(sm + S::kCcol);
+    int32_t *cend = reinterpret_cast<int32_t *>(sm + S::kCend);
+    int32_t *segq = reinterpret_cast<int32_t *>(sm + S::kSegQ);
+    int32_t *segoff = reinterpret_cast<int32_t *>(sm + S::kSegOff);
+    uint16_t *segt = reinterpret_cast<uint16_t *>(sm + S::kSegT);
+    int32_t *tlen = reinterpret_cast<int32_t *>(sm + S::kKeyA);   // segment search scratch
+    int32_t *tpos = reinterpret_cast<int32_t *>(sm + S::kKeyB);
+    BlockGrp<NT> g;
+    g.ws = ws;
     const uint64_t keep = l2_keep_policy();
-    const unsigned lt = (1u << lane) - 1u;
     const unsigned long long nspans = *reinterpret_cast<const unsigned long long *>(j.win_ctr);
     unsigned long long *taken = reinterpret_cast<unsigned long long *>(j.win_ctr) + 1;
 
+    TileCtx<P> x;
+    x.segq = segq;
+    x.segoff = segoff;
+    x.segt = segt;
+    x.bits = reinterpret_cast<uint32_t *>(sm + S::kBits);
+    x.wpre = reinterpret_cast<int32_t *>(sm + S::kWpre);
+    x.keyA = reinterpret_cast<uint32_t *>(sm + S::kKeyA);
+    x.keyB = reinterpret_cast<uint32_t *>(sm + S::kKeyB);
+    x.vals = reinterpret_cast<T *>(sm + S::kVals);
+    x.lidx = reinterpret_cast<uint16_t *>(sm + S::kLidx);
+    x.cnt = reinterpret_cast<uint16_t *>(sm + S::kCnt);
+    x.htop = reinterpret_cast<T *>(sm + S::kHTop);
+    x.hpend = reinterpret_cast<T *>(sm + S::kHPend);
+    x.hmask = reinterpret_cast<uint32_t *>(sm + S::kHMask);
+    x.hlast = reinterpret_cast<int32_t *>(sm + S::kHLast);
+    x.s_int = s_int;
+    x.ws = ws;
+    x.keep = keep;
+    x.err = j.err;
+
     for (;;) {
-        unsigned long long s = 0;
-        if (lane == 0) s = atomicAdd(taken, 1ull);
-        s = __shfl_sync(kFull, s, 0);
+        if (tid == 0) s_span = atomicAdd(taken, 1ull);
+        __syncthreads();
+        const unsigned long long s = s_span;
+        __syncthreads();
         if (s >= nspans) break;
         const int2 sp = j.win_spans[s];
         const int r = sp.x, row = j.rows[r];
@@ -667,16 +740,19 @@ __global__ void __launch_bounds__(kWinWarps * 32) k_long_win(RowJob j) {
         const int64_t rownnz = j.win_rownnz[r];
         const int64_t obase = j.out_rp[row];
         const int64_t slot = j.out_rp[row + 1] - obase;
-        if (sp.y == 0 && lane == 0 && (rownnz > slot || (j.exact && rownnz != slot))) atomicOr(j.err, 1u);
-        int32_t *ocol = j.out_col + obase;
-        Out *oval = static_cast<Out *>(j.out_val) + obase;
+        if (sp.y == 0 && tid == 0 && (rownnz > slot || (j.exact && rownnz != slot))) atomicOr(j.err, 1u);
         if (w0 >= w1) continue;
+        if (L > kTileMaxL) {
+            if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: the host gives such rows the merge rounds
+            continue;
+        }
+        x.aval = ri.aval;
+        x.bcol = ri.bcol;
+        x.bval = ri.bval;
 
-        // cursors at the span's first column (position, end of the list, the
-        // column at the position or INT_MAX); lane l owns lists l, l + 32, ...
-        int4 *cur = L <= kWinSmemL ? cur_s : cur_g;
+        // cursors at the span's first column
         const int cstart = wr[w0].c0;
-        for (int t = lane; t < L; t += 32) {
+        for (int t = tid; t < L; t += NT) {
             const int k = ri.acol[t];
             int lo = ri.brp[k];
             const int q1 = ri.brp[k + 1];
@@ -685,143 +761,186 @@ __global__ void __launch_bounds__(kWinWarps * 32) k_long_win(RowJob j) {
                 const int mid = (lo + hi) >> 1;
                 if (__ldg(ri.bcol + mid) < cstart) lo = mid + 1; else hi = mid;
             }
-            cur[t] = make_int4(lo, q1, lo < q1 ? __ldg(ri.bcol + lo) : INT_MAX, 0);
+            cpos[t] = lo;
+            cend[t] = q1;
+            ccol[t] = lo < q1 ? __ldg(ri.bcol + lo) : INT_MAX;
         }
+        __syncthreads();
 
+        const int J = (L + NT - 1) / NT;
+        const int t0 = min(L, tid * J), t1 = min(L, t0 + J);
         for (int w = w0; w < w1; ++w) {
             const WinRec rec = wr[w];
             if (rec.np == 0) continue;
             const int c0 = rec.c0;
             const int c1 = w + 1 < nwin ? wr[w + 1].c0 : INT_MAX;
-            const int64_t expect = (w + 1 < nwin ? wr[w + 1].off : rownnz) - rec.off;
-            const bool hot = rec.np > kWinP;
-            if (hot) {
-                uint32_t *gmask = reinterpret_cast<uint32_t *>(hs + H::kMask);
-                for (int c = lane; c < kWinCellMax; c += 32) gmask[c] = kWinEmpty;
-            }
-            int64_t count = 0;   // outputs written
-            int fill = 0, nseg = 0;
-            bits[lane] = 0u;
-            __syncwarp();
-            const WinCtx<P> cx{wb, hs, reinterpret_cast<T *>(hs + H::kClosed), ri.aval, ri.bcol, ri.bval, keep, c0,
-                               hot, ocol + rec.off, oval + rec.off, expect};
+            x.c0 = c0;
+            x.ocol = j.out_col + obase + rec.off;
+            x.oval = static_cast<Out *>(j.out_val) + obase + rec.off;
+            x.expect = (w + 1 < nwin ? wr[w + 1].off : rownnz) - rec.off;
+            if (rec.off + x.expect > slot) x.expect = rec.off < slot ? slot - rec.off : 0;   // flagged above
 
-            // segments: every list's elements in [c0, c1), in list order;
-            // kWinCurU cursors per lane are loaded before any is used
-            for (int tb = 0; tb < L; tb += 32 * kWinCurU) {
-                int4 cs[kWinCurU];
+            // 1. every list's segment below c1, numbered in list order; the
+            // next four columns of up to four lists are loaded at once
+            int ns = 0, np = 0;
+            for (int tq = t0; tq < t1; tq += 4) {
+                int cu[4][4], pos[4], hi[4];
 #pragma unroll
-                for (int u = 0; u < kWinCurU; ++u) {
-                    const int t = tb + 32 * u + lane;
-                    cs[u] = t < L ? cur[t] : make_int4(0, 0, INT_MAX, 0);
+                for (int u = 0; u < 4; ++u) {
+                    const int t = tq + u;
+                    pos[u] = -1;
+                    hi[u] = 0;
+                    if (t < t1) {
+                        const int col = ccol[t];
+                        if (col < c1) {
+                            pos[u] = cpos[t];
+                            hi[u] = (int)min((int64_t)cend[t], (int64_t)pos[u] + ((int64_t)c1 - col));
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        cu[u][v] = pos[u] >= 0 && pos[u] + 1 + v < hi[u] ? __ldg(ri.bcol + pos[u] + 1 + v) : INT_MAX;
                 }
 #pragma unroll
-                for (int u = 0; u < kWinCurU; ++u) {
-                    const int t = tb + 32 * u + lane;
-                    if (!__any_sync(kFull, cs[u].z < c1)) continue;
-                    int q = 0, len = 0;
-                    if (cs[u].z < c1) {
-                        int e = cs[u].x + 1, nx = INT_MAX;
-                        while (e < cs[u].y) {
-                            const int cc = __ldg(ri.bcol + e);
-                            if (cc >= c1) {
-                                nx = cc;
-                                break;
+                for (int u = 0; u < 4; ++u) {
+                    const int t = tq + u;
+                    if (t < t1) {
+                        int len = 0;
+                        if (pos[u] >= 0) {
+                            const int p = pos[u], end = cend[t];
+                            int e = -1, ncol = INT_MAX;
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                if (e < 0 && p + 1 + v < hi[u] && cu[u][v] >= c1) {
+                                    e = p + 1 + v;
+                                    ncol = cu[u][v];
+                                }
+                            if (e < 0) {
+                                e = tile_seg_end(ri.bcol, p + 4, hi[u], c1);
+                                ncol = e < end ? __ldg(ri.bcol + e) : INT_MAX;
                             }
-                            ++e;
+                            len = e - p;
+                            cpos[t] = e;
+                            ccol[t] = ncol;
+                            tpos[t] = p;
                         }
-                        q = cs[u].x;
-                        len = e - cs[u].x;
-                        cur[t] = make_int4(e, cs[u].y, nx, 0);
-                    }
-                    while (__any_sync(kFull, len > 0)) {
-                        int xs = len;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const int y = __shfl_up_sync(kFull, xs, d);
-                            if (lane >= d) xs += y;
-                        }
-                        const int tot = __shfl_sync(kFull, xs, 31);
-                        const int ex = xs - len;
-                        const int room = kWinP - fill;
-                        const int take = max(0, min(len, room - ex));
-                        const unsigned tm = __ballot_sync(kFull, take > 0);
-                        if (take > 0) {
-                            const int sg = nseg + __popc(tm & lt);
-                            const int p0 = fill + ex;
-                            segb[sg] = q - p0;
-                            segt[sg] = (uint16_t)t;
-                            atomicOr(&bits[p0 >> 5], 1u << (p0 & 31));
-                        }
-                        nseg += __popc(tm);
-                        fill += min(tot, room);
-                        q += take;
-                        len -= take;
-                        __syncwarp();
-                        if (fill == kWinP && (hot || __any_sync(kFull, len > 0))) {
-                            count += win_chunk<P>(cx, fill, count);
-                            fill = 0;
-                            nseg = 0;
-                        }
+                        tlen[t] = len;
+                        ns += len > 0 ? 1 : 0;
+                        np += len;
                     }
                 }
             }
-            if (fill > 0) count += win_chunk<P>(cx, fill, count);
+            int tns, tnp;
+            const int2 ex = tile_scan2(ns, np, tns, tnp, ws2);
+            {
+                int si = ex.x, po = ex.y;
+                for (int t = t0; t < t1; ++t) {
+                    const int len = tlen[t];
+                    if (len > 0) {
+                        segq[si] = tpos[t];
+                        segoff[si] = po;
+                        segt[si] = (uint16_t)t;
+                        ++si;
+                        po += len;
+                    }
+                }
+            }
+            if (tid == 0) {
+                segoff[tns] = tnp;
+                if (tnp != rec.np) atomicOr(j.err, 1u);
+            }
+            __syncthreads();
+            if (tnp == 0) continue;
 
-            if (hot) {
-                // every present column of the cell, in column order
-                __syncwarp();
-                T *gtop = reinterpret_cast<T *>(hs + H::kTop);
-                uint32_t *gmask = reinterpret_cast<uint32_t *>(hs + H::kMask);
-                T *gpend = reinterpret_cast<T *>(hs + H::kPend);
-                for (int cb = 0; cb < kWinCellMax; cb += 32) {
-                    const int c = cb + lane;
-                    const uint32_t gm = gmask[c];
-                    const bool has = gm != kWinEmpty;
-                    T v = T();
-                    if (has) {
-                        const WinStack<P, T *> g{gpend + c, kWinCellMax, gtop[c], gm, 0};
-                        v = g.finish();
-                    }
-                    const unsigned msk = __ballot_sync(kFull, has);
-                    if (has) {
-                        const int64_t wpos = count + __popc(msk & lt);
-                        if (wpos < expect) {
-                            __stcs(ocol + rec.off + wpos, (int32_t)(c0 + c));
-                            __stcs(oval + rec.off + wpos, P::fin(v));
-                        }
-                    }
-                    count += __popc(msk);
-                }
-                __syncwarp();
+            if (tnp <= kTileP) {
+                const int nout = tile_chunk<P>(x, 0, tns, 0, tnp, false, 0);
+                if (tid == 0 && nout != x.expect) atomicOr(j.err, 1u);
+                continue;
             }
-            if (lane == 0 && count != expect) atomicOr(j.err, 1u);
+            // 2. a hot tile: chunks of aligned list blocks, every column's
+            // chunk sums added by its carried stack
+            for (int c = tid; c < kWinCellMax; c += NT) x.hmask[c] = kWinEmpty;
+            int cur = 0;
+            while (cur < L) {
+                if (tid == 0) {
+                    // first segment of a list >= t
+                    auto seg_at = [&](int t) {
+                        int lo = 0, hi = tns;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((int)segt[mid] < t) lo = mid + 1; else hi = mid;
+                        }
+                        return lo;
+                    };
+                    int k = cur == 0 ? kTileLevels : min(__ffs(cur) - 1, kTileLevels);
+                    const int sa = seg_at(cur);
+                    int sb = sa;
+                    for (;; --k) {
+                        sb = seg_at(min(L, cur + (1 << k)));
+                        if (segoff[sb] - segoff[sa] <= kTileP || k == 0) break;
+                    }
+                    s_chunk[0] = sa;
+                    s_chunk[1] = sb;
+                    s_chunk[2] = min(L, cur + (1 << k));
+                    s_chunk[3] = cur;
+                }
+                __syncthreads();
+                const int sa = s_chunk[0], sb = s_chunk[1], nxt = s_chunk[2], tb = s_chunk[3];
+                const int pos0 = segoff[sa], n = segoff[sb] - pos0;
+                __syncthreads();   // s_chunk is rewritten next
+                if (n > kTileP) {
+                    if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: one list holds at most one cell
+                } else if (n > 0) {
+                    tile_chunk<P>(x, sa, sb, pos0, n, true, tb);
+                }
+                cur = nxt;
+            }
+            // the columns of the cell in order
+            __syncthreads();
+            bool has = false;
+            T v = T();
+            if (tid < kWinCellMax) {
+                const uint32_t hm = x.hmask[tid];
+                has = hm != kWinEmpty;
+                if (has) {
+                    const WinStack<P, T *> st{x.hpend + tid, kWinCellMax, x.htop[tid], hm, 0};
+                    v = st.finish();
+                }
+            }
+            int tot;
+            const int wpos = g.scan_excl(has ? 1 : 0, tot);
+            if (has && wpos < x.expect) {
+                __stcs(x.ocol + wpos, (int32_t)(c0 + tid));
+                __stcs(x.oval + wpos, P::fin(v));
+            }
+            if (tid == 0 && tot != x.expect) atomicOr(j.err, 1u);
+            __syncthreads();
         }
+        __syncthreads();   // the cursors are reloaded for the next span
     }
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// Blocks of the numeric kernel: every SM's resident blocks (the per-warp
-// scratch is allocated for exactly this many).
+// Blocks of the numeric kernel: every SM's resident blocks.
 template <class P>
 int win_grid_t() {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t sm = kWinWarps * WinSmem<P>::kBytes;
-    if (cudaFuncSetAttribute(k_long_win<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_long_win<P>, kWinWarps * 32, sm) != cudaSuccess) {
+    const size_t sm = TileSmem<P>::kBytes;
+    if (cudaFuncSetAttribute(k_long_tile<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_long_tile<P>, kTileThreads, sm) != cudaSuccess) {
         cudaGetLastError();
         occ = 1;
     }
     return std::max(sms, 1) * std::max(occ, 1);
 }
 
-// The long rows of one pass by column windows: the plan (when this pass makes
+// The long rows of one pass by column tiles: the plan (when this pass makes
 // it: the symbolic pass, or BRMerge-Upper's numeric pass), then -- for a
-// value pass -- the windows.
+// value pass -- the tiles.
 template <class P>
 cudaError_t launch_long_win(const RowJob &j, cudaStream_t st) {
     cudaError_t e;
@@ -836,19 +955,15 @@ cudaError_t launch_long_win(const RowJob &j, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if constexpr (P::kVal) {
-        const size_t sm = kWinWarps * WinSmem<P>::kBytes;
-        auto kw = k_long_win<P>;
+        const size_t sm = TileSmem<P>::kBytes;
+        auto kw = k_long_tile<P>;
         if ((e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(j.win_ctr + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-        kw<<<j.win_grid, kWinWarps * 32, sm, st>>>(j);
+        kw<<<j.win_grid, kTileThreads, sm, st>>>(j);
         g_launches.fetch_add(1, std::memory_order_relaxed);
     }
     return cudaGetLastError();
 }
-
-// Bytes of the per-warp scratch of the numeric kernel.
-template <class P>
-__host__ __device__ constexpr size_t win_hot_bytes() { return WinHot<P>::kBytes; }
 
 }  // namespace brm

@@ -1,16 +1,19 @@
-"""Long rows by column windows (option long_window).
+"""Long rows by column tiles (option long_window).
 
-A long row is cut into column windows planned from the symbolic pass's
-bitmap and per-cell product histogram; every window's products are sorted in
-registers and each column is summed in the merge tree's order, windows of a
-single crowded cell in chunks with every column's partial sums carried
-between them.  The result must be the merge rounds' bits and the oracle's
-Algorithm 1 in every precision.  The cases reach: windows of many cells and
-of one cell, hot cells with runs of up to 65535 products (many chunks),
-spans of several windows, B wider than one bitmap window of 2^20 columns,
-rows past the 65535-list limit (merge rounds instead), BRMerge-Upper (the
-plan made in the numeric pass), batched products and a prepared batch
-replayed from a CUDA graph.
+A long row of at most 2048 lists is cut into column tiles planned from the
+symbolic pass's bitmap and per-cell product histogram; every tile's products
+are sorted by column in shared memory (a stable radix sort that keeps list
+order) and Algorithm 1's merge rounds run on the sorted positions; a single
+crowded cell of more than 2048 products is taken in chunks of aligned list
+blocks, every column's chunk sums carried between them.  Rows of more lists
+keep the merge rounds in the same pass.  The result must be the merge
+rounds' bits and the oracle's Algorithm 1 in every precision.  The cases
+reach: tiles of many cells and of one cell, hot cells with runs of up to
+2048 products (many chunks), a single run that fills a tile, spans of
+several tiles, B wider than one bitmap window of 2^20 columns, rows past the
+2048-list limit (merge rounds instead, alone and mixed with tiled rows),
+BRMerge-Upper (the plan made in the numeric pass), batched products and a
+prepared batch replayed from a CUDA graph.
 """
 import numpy as np
 import pytest
@@ -78,7 +81,7 @@ def test_windows_match_rounds_and_oracle(mode, dtype, comp):
 
 def test_windows_are_taken():
     """With long_window the long rows run as the plan (symbolic pass) and one
-    window launch (numeric pass)."""
+    tile launch (numeric pass)."""
     R = I.rmat(12, 16, seed=85)
     assert long_trace(R, R) == (1, 1)
     sym, num = long_trace(R, R, long_window=False)
@@ -88,15 +91,16 @@ def test_windows_are_taken():
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
 @pytest.mark.parametrize("ncols", [4096, 1 << 20])
 def test_hot_cells(mode, dtype, comp, ncols):
-    """Columns 0..3 in most of up to 65535 lists: single-cell windows far
-    beyond one sort (runs of up to 65535 products, dozens of chunks), a cell
-    of warm columns, cold columns spread wide.  With 4096 columns every cell
-    is one column wide; with 2^20, 128."""
+    """Columns 0..3 in most of up to 2048 lists: single-cell tiles far beyond
+    one sort (runs of up to 2048 products, many chunks of aligned list
+    blocks), a cell of warm columns, cold columns spread wide; one row of 5000
+    lists keeps the merge rounds.  With 4096 columns every cell is one column
+    wide; with 2^20, 128."""
     k = 70000
     hot_cols = [0, 1, 2, 3] + list(range(16, 200, 3))
     hot_p = [0.97, 0.5, 0.08, 0.03] + [0.01] * (len(hot_cols) - 4)
     B = hot_b(k, ncols, 91, hot_cols, hot_p, 3)
-    A = rows_of_a([65535, 20000, 5000, 4500, 3000, 600, 1], k, 92)
+    A = rows_of_a([2048, 2047, 1500, 1025, 5000, 600, 1], k, 92)
     ref = oracle.alg1(A, B, prec=mode)
     C = run(A, B, "precise", dtype, comp)
     assert_rows_exact(C, ref)
@@ -107,17 +111,20 @@ def test_hot_cells(mode, dtype, comp, ncols):
 
 
 def test_windows_degenerate_rows():
-    """Every list the same one column (a hot window holding a single run of
-    9000 products), one list of 10000 products, two identical lists, and a
-    row of 3001 lists of which only one is not empty."""
-    k, ncols = 15000, 300000
-    one = [np.array([777])] * 9000
+    """Every list the same one column (one run of 2048 products filling a
+    tile; 2045 of them and three more lists, a hot tile), one list of 10000
+    products, two identical lists, a row of 2000 lists of which only one is
+    not empty, and a row of 2049 lists (merge rounds)."""
+    k, ncols = 6000, 300000
+    one = [np.array([777])] * 2048
     wide = [np.arange(0, 300000, 30)]
     pair = [np.arange(5, 300000, 50)] * 2
-    B = csr_from_rows(one + wide + pair + [np.array([1, 2])] * 2997 + [np.zeros(0, np.int64)] * 3000, ncols, 93, 1)
+    B = csr_from_rows(one + wide + pair + [np.array([1, 2])] * 949 + [np.zeros(0, np.int64)] * 3000, ncols, 93, 1)
     assert B.rows == k
-    A = csr_from_rows([np.arange(9000), np.array([9000]), np.array([9001, 9002]), np.arange(8990, 9003),
-                       np.concatenate([np.arange(9000, 9001), np.arange(k - 3000, k)])], k, 94, 2)
+    A = csr_from_rows([np.arange(2048), np.concatenate([np.arange(2045), [2048, 2049, 2050]]), np.array([2048]),
+                       np.array([2049, 2050]), np.arange(2040, 2051),
+                       np.concatenate([np.arange(2048, 2049), np.arange(k - 1999, k)]), np.arange(1000, 3049)],
+                      k, 94, 2)
     ref = oracle.alg1(A, B)
     for kw in ({}, {"long_window": False}):
         assert_rows_exact(run(A, B, **kw), ref)
@@ -140,14 +147,23 @@ def test_windows_wide_B_several_bitmap_windows():
 
 
 def test_windows_list_limit_uses_merge_rounds():
-    """A row of 70000 lists is past the windows' 16-bit list index: the pass
-    keeps the merge rounds, with the same result."""
+    """Rows of more than 2048 lists keep the merge rounds: alone (one
+    symbolic launch, the column bitmap), and mixed with tiled rows in the
+    same passes (the plan and the bitmap, the tiles and the rounds)."""
     k, ncols = 70000, 50000
     B = hot_b(k, ncols, 97, [10, 11], [0.3, 0.3], 2)
     A = rows_of_a([70000, 5000, 10], k, 98)
     assert_rows_exact(run(A, B), oracle.alg1(A, B))
     sym, num = long_trace(A, B)
     assert sym == 1 and num >= 1
+    A2 = rows_of_a([2049, 2048, 4000, 1500, 300], k, 108)
+    ref = oracle.alg1(A2, B)
+    C = run(A2, B)
+    assert_rows_exact(C, ref)
+    same(C, run(A2, B, long_window=False))
+    assert_rows_exact(run(A2, B, "upper"), ref)
+    sym, num = long_trace(A2, B)
+    assert sym == 2 and num >= 2
 
 
 def test_windows_batched_and_graph_replay():
