@@ -161,15 +161,20 @@ typedef struct {
  *                  32 GiB, per chunk).  A smaller budget runs fewer
  *                  persistent blocks (merge rounds) or more batches (column
  *                  buckets).
- *   long_window    1: rows beyond block_max_nprod are cut into column
- *                  windows of at most 1024 products (the symbolic pass plans
- *                  them from a column bitmap and a product histogram), spread
- *                  over many warps, each window's keys sorted in registers by
- *                  one warp and every column summed in the merge tree's order
- *                  (the same values as the merge rounds), when long_bucket is
- *                  0, B has at most 2^24 columns and every such row at most
- *                  65535 lists (BRMerge-Upper in row chunks keeps the merge
- *                  rounds); 0 (default): the arena merge rounds.
+ *   long_window    how rows beyond block_max_nprod are merged when
+ *                  long_bucket is 0 and B has at most 2^24 columns.  1
+ *                  (default): rows of at most 2048 lists and at least 65536
+ *                  products are cut into column tiles of at most 2048
+ *                  products (the symbolic pass plans them from a column
+ *                  bitmap and a per-cell product histogram), each tile's
+ *                  products sorted by column in shared memory and summed by
+ *                  Algorithm 1's merge rounds on the sorted positions, one
+ *                  thread block per tile (the same values as the merge rounds
+ *                  in the arena); other long rows take the arena merge rounds
+ *                  in the same pass.  2: every long row of at most 2048 lists
+ *                  takes the tiles.  0: every long row takes the arena merge
+ *                  rounds.  BRMerge-Upper in row chunks always takes the
+ *                  arena merge rounds.
  *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
  *                  sizeof value) bytes) processed at once; a larger product
  *                  is processed in row chunks of at most this size, each

@@ -251,7 +251,7 @@ def _stream(stream=None):
 def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod=0, reg_max_nprod=0,
             reg_keys=0, reg_warps=0, symbolic_hash=False, reg_top=True, reg_perm=True, reg_num_half=True,
             reg_num_direct=True, long_bucket=False, arena_bytes=0, upper_chunk_bytes=0,
-            long_window=False) -> brm_options:
+            long_window=None) -> brm_options:
     o = brm_options()
     load().brm_options_default(ctypes.byref(o))
     o.validate = int(bool(validate))
@@ -274,7 +274,9 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
     o.long_bucket = int(bool(long_bucket))
     o.arena_bytes = arena_bytes
     o.upper_chunk_bytes = upper_chunk_bytes
-    o.long_window = int(bool(long_window))
+    if long_window is not None:
+        # True: every long row of at most 2048 lists takes the column tiles
+        o.long_window = long_window if type(long_window) is int else (2 if long_window else 0)
     return o
 
 

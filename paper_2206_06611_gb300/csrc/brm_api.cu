@@ -248,7 +248,7 @@ brm_options resolve(const brm_options *o) {
     r.reg_num_half = r.reg_num_half != 0 ? 1 : 0;
     r.reg_num_direct = r.reg_num_direct != 0 ? 1 : 0;
     r.long_bucket = r.long_bucket != 0 ? 1 : 0;
-    r.long_window = r.long_window != 0 ? 1 : 0;
+    r.long_window = r.long_window < 0 || r.long_window > 2 ? 1 : r.long_window;
     if (r.reg_max_nprod < 0) r.reg_max_nprod = 0;
     return r;
 }
@@ -385,18 +385,21 @@ int make_plan(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t 
         BRM_CUDA(cudaMemcpyAsync(Ls.data(), pl.long_L, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, mem.st));
         BRM_CUDA(cudaStreamSynchronize(mem.st));
         // largest rows first, so that the longest merges start earliest; with
-        // column tiles, the rows of more than kTileMaxL lists (merge rounds)
-        // before the others
+        // column tiles, the rows that keep the merge rounds (more than
+        // kTileMaxL lists, or -- long_window 1 -- fewer than kTileMinNprod
+        // products) before the others
         const bool tiles = tiles_apply(o, src.bcols);
+        const int64_t tmin = o.long_window == 1 ? kTileMinNprod : 0;
+        auto rounds = [&](int64_t x) { return !tiles || Ls[x] > kTileMaxL || np[x] < tmin; };
         std::vector<int64_t> idx(nl);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
-            const bool rx = !tiles || Ls[x] > kTileMaxL, ry = !tiles || Ls[y] > kTileMaxL;
+            const bool rx = rounds(x), ry = rounds(y);
             if (rx != ry) return rx;
             return np[x] > np[y];
         });
         pl.long_split = 0;
-        for (int64_t s = 0; s < nl; ++s) pl.long_split += (!tiles || Ls[s] > kTileMaxL) ? 1 : 0;
+        for (int64_t s = 0; s < nl; ++s) pl.long_split += rounds(s) ? 1 : 0;
         pl.long_rows_h.resize(nl);
         pl.long_nprod_h.resize(nl);
         pl.long_L_h.resize(nl);
@@ -1221,7 +1224,7 @@ void brm_options_default(brm_options *o) {
     o->long_bucket = 0;
     o->symbolic_hash = 0;
     o->arena_bytes = 0;
-    o->long_window = 0;
+    o->long_window = 1;
 }
 
 const char *brm_last_error(void) { return g_err.c_str(); }

@@ -68,12 +68,15 @@ __host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUn
 // cell of at most kWinCellMax columns (a "hot" tile, taken in chunks); the
 // plan cuts pieces every kWinH products and packs them into tiles; at most
 // kWinCells cells per bitmap window of kWinBitmapCols columns; rows of at most
-// kTileMaxL lists (longer ones keep the merge rounds); spans of at least
+// kTileMaxL lists and at least kTileMinNprod products (others keep the merge
+// rounds); spans of at least
 // max(kWinSpanMin, kWinSpanPerList * L) products.
 constexpr int kTileP = 2048;
 constexpr int kTilePBits = 11;
 constexpr int kTileThreads = 256;
 constexpr int kTileMaxL = 2048;
+// long rows of fewer products keep the merge rounds (measured faster there)
+constexpr int64_t kTileMinNprod = 65536;
 constexpr int kWinH = 256;
 constexpr int64_t kWinBitmapCols = (int64_t)1 << 20;
 constexpr int kWinCells = 8192;
@@ -83,7 +86,7 @@ constexpr int kWinSpanPerList = 16;
 static_assert((1 << kTilePBits) == kTileP, "a tile position fits the key's low bits");
 static_assert(kTileMaxL <= kTileP, "one column of a tile holds at most kTileMaxL products");
 static_assert(kWinCellMax == 128, "cells are at most 128 columns wide");
-static_assert((kWinBitmapCols << kTilePBits) <= ((int64_t)1 << 32) - 1, "key = column offset and position");
+static_assert((((kWinBitmapCols - 1) << kTilePBits) | (kTileP - 1)) <= 0xffffffffLL, "key = column offset and position");
 
 // One window of a long row: first column, products, and the number of the
 // row's distinct columns before it (its output offset inside the row).

@@ -317,7 +317,9 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_long_sym(RowJob j) {
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
-                            if (q[k] >= 0 && c[k] >= 0 && u < wn) atomicOr(&bm[u >> 5], 1u << (u & 31));
+                            // a column already set needs no atomic (hub columns recur in many lists)
+                            if (q[k] >= 0 && c[k] >= 0 && u < wn && !(bm[u >> 5] & (1u << (u & 31))))
+                                atomicOr(&bm[u >> 5], 1u << (u & 31));
                         }
                     }
                 }

@@ -34,7 +34,7 @@
 //      c1 - column: B's columns are distinct), segments numbered in list
 //      order;
 //   2. the products are formed in that order -- position p in list order --
-//      with 32-bit keys ((column - c0) << 11) | p;
+//      with 32-bit keys ((column - c0) << kTilePBits) | p;
 //   3. a stable radix sort by column (8-bit digits, as many passes as the
 //      tile's columns need) puts every column's products together, still in
 //      list order;
@@ -87,7 +87,9 @@ constexpr uint16_t kTileRet = 0x8000u;         // a retired position of the merg
 static_assert(kTileP < kTileRet, "positions fit 15 bits");
 constexpr int kTileNW = kTileThreads / 32;
 constexpr int kTileQ = kTileP / kTileThreads;   // sorted positions per thread
-static_assert(kTileThreads == 256, "one radix digit per thread");
+static_assert(kTileThreads >= 256 && kTileThreads % 256 == 0, "a radix digit per thread of the first 256");
+constexpr int kTileWords = kTileP / 32;            // words of a position bitmap
+static_assert(kTileWords % 32 == 0, "whole words per lane");
 
 // ---------------------------------------------------------------------------
 // Plan
@@ -124,21 +126,26 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                 const int ncl = min(NT, ri.L - t0);
                 const int tot = lb_load_chunk<float, NT>(g, ri, t0, s_q0, s_off, nullptr);
                 for (int base = 0; base < tot; base += NT * K) {
+                    // every lane takes part (the warp's equal cells are counted
+                    // with one add); lanes past the products hold none
                     const int p0 = base + tid * K;
-                    if (p0 < tot) {
-                        int tl[K], q[K];
-                        lb_locate<K>(s_off, s_q0, ncl, tot, p0, tl, q);
-                        int32_t c[K];
+                    int tl[K], q[K];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) c[k] = q[k] >= 0 ? __ldg(ri.bcol + q[k]) : -1;
+                    for (int k = 0; k < K; ++k) q[k] = -1;
+                    if (p0 < tot) lb_locate<K>(s_off, s_q0, ncl, tot, p0, tl, q);
+                    int32_t c[K];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
-                            if (q[k] >= 0 && c[k] >= 0 && u < wn) {
-                                atomicOr(&bm[u >> 5], 1u << (u & 31));
-                                atomicAdd(&hist[u >> sh], 1u);
-                            }
-                        }
+                    for (int k = 0; k < K; ++k) c[k] = q[k] >= 0 ? __ldg(ri.bcol + q[k]) : -1;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
+                        const bool in = q[k] >= 0 && c[k] >= 0 && u < wn;
+                        // a column already set needs no atomic (hub columns
+                        // recur in many lists)
+                        if (in && !(bm[u >> 5] & (1u << (u & 31)))) atomicOr(&bm[u >> 5], 1u << (u & 31));
+                        const int cell = in ? (int)(u >> sh) : -1;
+                        const unsigned peers = __match_any_sync(0xffffffffu, cell);
+                        if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[cell], (unsigned)__popc(peers));
                     }
                 }
                 g.sync();
@@ -345,8 +352,8 @@ struct TileSmem {
     static constexpr size_t kKeyB = kKeyA + 4 * kTileP;                             // uint32[kTileP]
     static constexpr size_t kVals = kKeyB + 4 * kTileP;                             // T[kTileP]
     static constexpr size_t kLidx = kVals + sizeof(T) * kTileP;                     // uint16[kTileP]
-    static constexpr size_t kCnt = align_up(kLidx + 2 * kTileP, 16);                // uint16[kTileNW][256]
-    static constexpr size_t kHTop = align_up(kCnt + 2 * kTileNW * 256, 16);         // T[kWinCellMax]
+    static constexpr size_t kCnt = align_up(kLidx + 2 * kTileP, 16);                // uint32[kTileNW][256]
+    static constexpr size_t kHTop = align_up(kCnt + 4 * kTileNW * 256, 16);         // T[kWinCellMax]
     static constexpr size_t kHPend = kHTop + sizeof(T) * kWinCellMax;               // T[kTileLevels][kWinCellMax]
     static constexpr size_t kHMask = kHPend + sizeof(T) * kTileLevels * kWinCellMax;   // uint32[kWinCellMax]
     static constexpr size_t kHLast = kHMask + 4 * kWinCellMax;                      // int32[kWinCellMax]
@@ -394,57 +401,95 @@ __device__ __forceinline__ int2 tile_scan2(int a, int b, int &ta, int &tb, int2 
 
 // One pass of a stable radix sort of n <= kTileP keys by the 8-bit digit at
 // `shift`: warp w ranks keys [w * kTileQ * 32, (w + 1) * kTileQ * 32) in
-// order (lanes with equal digits found by __match_any_sync), the digit
-// offsets are laid out digit-major and warp-minor, and every key moves to
-// its digit's offset plus its rank.
-__device__ __forceinline__ void tile_radix_pass(const uint32_t *src, uint32_t *dst, int n, int shift, uint16_t *cnt,
+// order -- the lanes with equal digits found by __match_any_sync, the lowest
+// of them adding their number to the warp's digit counter; the warp's kTileQ
+// steps add in turn (a warp barrier between them), so each step's old value
+// counts the equal digits of the steps before it -- the digit
+// offsets are laid out digit-major and warp-minor, and every key moves to its
+// digit's offset plus its rank.
+__device__ __forceinline__ void tile_radix_pass(const uint32_t *src, uint32_t *dst, int n, int shift, uint32_t *cnt,
                                                 int *ws) {
     BlockGrp<kTileThreads> g;
     g.ws = ws;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < kTileNW * 256; i += kTileThreads) cnt[i] = 0;
+    for (int i = tid; i < kTileNW * 256; i += kTileThreads) cnt[i] = 0u;
     __syncthreads();
-    uint16_t *wc = cnt + w * 256;
+    uint32_t *wc = cnt + w * 256;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[kTileQ];
-    int rk[kTileQ];
+    int dg[kTileQ], rk[kTileQ], ld[kTileQ];
+    unsigned pe[kTileQ];
 #pragma unroll
     for (int it = 0; it < kTileQ; ++it) {
         const int idx = w * (32 * kTileQ) + it * 32 + lane;
         const bool ok = idx < n;
         key[it] = ok ? src[idx] : 0u;
-        const int d = ok ? (int)((key[it] >> shift) & 255u) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int before = ok ? (int)wc[d] : 0;
-        rk[it] = before + __popc(peers & lt);
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wc[d] = (uint16_t)(before + __popc(peers));
-        __syncwarp();
+        dg[it] = ok ? (int)((key[it] >> shift) & 255u) : 256;
+        pe[it] = __match_any_sync(0xffffffffu, dg[it]);
+        ld[it] = __ffs(pe[it]) - 1;
     }
+#pragma unroll
+    for (int it = 0; it < kTileQ; ++it) {
+        uint32_t old = 0u;
+        if (dg[it] < 256 && lane == ld[it]) old = atomicAdd(&wc[dg[it]], (uint32_t)__popc(pe[it]));
+        rk[it] = (int)old;
+        __syncwarp();   // orders the steps' adds to a counter
+    }
+#pragma unroll
+    for (int it = 0; it < kTileQ; ++it) rk[it] = __shfl_sync(0xffffffffu, rk[it], ld[it]) + __popc(pe[it] & lt);
     __syncthreads();
     {
-        // thread tid lays out digit tid
-        int c[kTileNW], tot = 0;
+        // thread tid < 256 lays out digit tid
+        uint32_t c[kTileNW];
+        int tot = 0;
 #pragma unroll
         for (int v = 0; v < kTileNW; ++v) {
-            c[v] = cnt[v * 256 + tid];
-            tot += c[v];
+            c[v] = tid < 256 ? cnt[v * 256 + tid] : 0u;
+            tot += (int)c[v];
         }
         int all;
         int base = g.scan_excl(tot, all);
+        if (tid < 256) {
 #pragma unroll
-        for (int v = 0; v < kTileNW; ++v) {
-            cnt[v * 256 + tid] = (uint16_t)base;
-            base += c[v];
+            for (int v = 0; v < kTileNW; ++v) {
+                cnt[v * 256 + tid] = (uint32_t)base;
+                base += (int)c[v];
+            }
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < kTileQ; ++it) {
-        const int idx = w * (32 * kTileQ) + it * 32 + lane;
-        if (idx < n) dst[(int)wc[(key[it] >> shift) & 255u] + rk[it]] = key[it];
-    }
+    for (int it = 0; it < kTileQ; ++it)
+        if (dg[it] < 256) dst[(int)wc[dg[it]] + rk[it]] = key[it];
     __syncthreads();
+}
+
+// Exclusive prefix of the set bits of words [0, nw) of a position bitmap
+// (nw <= kTileWords) into pre, by one warp: lane l takes words
+// l * kTileWords / 32 .. + kTileWords / 32 - 1.
+__device__ __forceinline__ void tile_word_prefix(const uint32_t *bits, int32_t *pre, int nw) {
+    constexpr int PW = kTileWords / 32;
+    const int lane = threadIdx.x & 31;
+    int c[PW], v = 0;
+#pragma unroll
+    for (int u = 0; u < PW; ++u) {
+        const int i = lane * PW + u;
+        c[u] = i < nw ? __popc(bits[i]) : 0;
+        v += c[u];
+    }
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    int ex = incl - v;
+#pragma unroll
+    for (int u = 0; u < PW; ++u) {
+        const int i = lane * PW + u;
+        if (i < nw) pre[i] = ex;
+        ex += c[u];
+    }
 }
 
 // What the chunk step of a tile needs (shared memory, the row, the tile).
@@ -460,7 +505,7 @@ struct TileCtx {
     uint32_t *keyA, *keyB;
     T *vals;
     uint16_t *lidx;
-    uint16_t *cnt;
+    uint32_t *cnt;
     T *htop, *hpend;
     uint32_t *hmask;
     int32_t *hlast;
@@ -527,21 +572,9 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
         atomicOr(&x.bits[st >> 5], 1u << (st & 31));
     }
     __syncthreads();
-    if (wid == 0) {
-        const int i0 = 2 * lane, i1 = 2 * lane + 1;
-        const int p0 = i0 < nw ? __popc(x.bits[i0]) : 0, p1 = i1 < nw ? __popc(x.bits[i1]) : 0;
-        int v = p0 + p1;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int u = __shfl_up_sync(kFull, v, d);
-            if (lane >= d) v += u;
-        }
-        const int ex = v - p0 - p1;
-        if (i0 < nw) x.wpre[i0] = ex;
-        if (i1 < nw) x.wpre[i1] = ex + p0;
-    }
+    if (wid == 0) tile_word_prefix(x.bits, x.wpre, nw);
     __syncthreads();
-    // 2. the products in list order: key ((column - c0) << 11) | position
+    // 2. the products in list order: key ((column - c0) << kTilePBits) | position
     {
         int q[kTileQ], t[kTileQ];
 #pragma unroll
@@ -605,75 +638,101 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     // column have distinct t >> (h - 1), t the smallest list of the sum.
     // Round h adds to every live sum the next live sum of its column when
     // both have the same t >> h (the left one first) and retires the right
-    // one.  Two sums that meet in round h are neighbours among the live sums
-    // of their column: a retired position is never read again, and a sum
-    // that takes a partner is never taken in the same round (three live sums
+    // one.  A live sum and its next live sum of the same column therefore
+    // meet in round bitlen(t_left ^ t_right), and nothing changes that round
+    // before it: the right one can be retired only by its left neighbour, and
+    // the left one gets a new neighbour only by taking this one.  Each
+    // position keeps that level (15: no next sum in its column) and
+    // round h handles just the positions whose level is h; after taking its
+    // neighbour, a sum meets the next one in a later round (three live sums
     // of one column cannot share t >> h).  The leftmost sum of a column is
     // never retired: it ends as the column's value.
     uint16_t *nxt = reinterpret_cast<uint16_t *>(dst);           // next live position (kTileRet: retired)
     uint16_t *st = nxt + kTileP;                                  // smallest list of the sum at a position
-    BlockGrp<kTileThreads> g;
-    g.ws = x.ws;
-    const int s0 = tid * kTileQ;
-    uint32_t stm = 0, live = 0;
+    uint32_t *rs = x.bits;                                        // run starts, one bit per position
+    int32_t *rpre = x.wpre;                                       // run starts before every word
+    // thread tid owns positions tid + kTileThreads * i, with their meeting
+    // levels in the nibbles of lv; warp w's lanes cover the word i * kTileNW +
+    // w of the run-start bitmap
+    uint32_t ck[kTileQ];   // the owned sorted keys
 #pragma unroll
     for (int i = 0; i < kTileQ; ++i) {
-        const int s = s0 + i;
+        const int s = tid + kTileThreads * i;
+        ck[i] = kKeyPad;
         if (s < n) {
-            const uint32_t k = K[s];
-            st[s] = x.lidx[k & kTilePMask];
+            ck[i] = K[s];
+            st[s] = x.lidx[ck[i] & kTilePMask];
             nxt[s] = (uint16_t)(s + 1);
-            live |= 1u << i;
-            if (s == 0 || (K[s - 1] >> kTilePBits) != (k >> kTilePBits)) stm |= 1u << i;
         }
-    }
-    int nruns;
-    const int rbase = g.scan_excl(__popc(stm), nruns);   // its barriers publish nxt and st
-    const int hmax = tile_bitlen((uint32_t)(x.segt[sa] ^ x.segt[sb - 1]));
-    for (int h = 1; h <= hmax; ++h) {
-        uint32_t m = live;
-        while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            const int s = s0 + i;
-            const int j = nxt[s];
-            const uint32_t ks = K[s];
-            if ((j & kTileRet) || j >= n || (K[j] >> kTilePBits) != (ks >> kTilePBits)) {
-                // retired, or the last live sum of its column: no partner ever
-                live &= ~(1u << i);
-                continue;
-            }
-            if ((st[s] >> h) != (st[j] >> h)) continue;
-            const int ps = (int)(ks & kTilePMask), pj = (int)(K[j] & kTilePMask);
-            x.vals[ps] = P::add(x.vals[ps], x.vals[pj]);
-            nxt[s] = nxt[j];
-            nxt[j] = (uint16_t)(nxt[j] | kTileRet);
-        }
-        if (!__syncthreads_or(live != 0u)) break;
     }
     __syncthreads();
-    // 5. the columns' values
-    int ridx = rbase;
-    while (stm) {
-        const int i = __ffs(stm) - 1;
-        stm &= stm - 1u;
-        const uint32_t k = K[s0 + i];
-        tile_emit<P>(x, hot, tb, ridx, k >> kTilePBits, x.vals[k & kTilePMask]);
-        ++ridx;
+    uint32_t lv = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < kTileQ; ++i) {
+        const int s = tid + kTileThreads * i;
+        bool start = false;
+        if (s < n) {
+            start = s == 0 || (K[s - 1] >> kTilePBits) != (ck[i] >> kTilePBits);
+            if (s + 1 < n && (K[s + 1] >> kTilePBits) == (ck[i] >> kTilePBits)) {
+                const uint32_t m = (uint32_t)tile_bitlen((uint32_t)(st[s] ^ st[s + 1]));
+                lv = (lv & ~(15u << (4 * i))) | (m << (4 * i));
+            }
+        }
+        const unsigned b = __ballot_sync(kFull, start);
+        if (lane == 0) rs[i * kTileNW + wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) tile_word_prefix(rs, rpre, kTileWords);
+    for (int h = 1; h <= 15 && __syncthreads_or(lv != 0xffffffffu); ++h) {
+        // owned positions whose level is h: the zero nibbles of lv ^ h...h
+        const uint32_t e = lv ^ (0x11111111u * (uint32_t)h);
+        uint32_t z = ~(((e & 0x77777777u) + 0x77777777u) | e) & 0x88888888u;
+        while (z) {
+            const int bit = __ffs(z) - 1;
+            z &= z - 1u;
+            const int i = bit >> 2;
+            const int s = tid + kTileThreads * i;
+            const int j = nxt[s];
+            if (j & kTileRet) {   // retired by its left neighbour: it meets nothing any more
+                lv |= 15u << (4 * i);
+                continue;
+            }
+            const uint32_t kss = K[s], kjj = K[j];
+            const int ps = (int)(kss & kTilePMask), pj = (int)(kjj & kTilePMask);
+            x.vals[ps] = P::add(x.vals[ps], x.vals[pj]);
+            const int k = nxt[j];
+            nxt[s] = (uint16_t)k;
+            nxt[j] = (uint16_t)(k | kTileRet);
+            uint32_t m = 15u;
+            if (k < n && (K[k] >> kTilePBits) == (kss >> kTilePBits))
+                m = (uint32_t)tile_bitlen((uint32_t)(st[s] ^ st[k]));
+            lv = (lv & ~(15u << (4 * i))) | (m << (4 * i));
+        }
+    }
+    __syncthreads();
+    // 5. the columns' values: a column's output is the rank of its first position
+    const int nruns = rpre[kTileWords - 1] + __popc(rs[kTileWords - 1]);
+#pragma unroll
+    for (int i = 0; i < kTileQ; ++i) {
+        const int s = tid + kTileThreads * i;
+        if ((rs[s >> 5] >> (s & 31)) & 1u) {
+            const int ridx = rpre[s >> 5] + __popc(rs[s >> 5] & ((1u << (s & 31)) - 1u));
+            tile_emit<P>(x, hot, tb, ridx, ck[i] >> kTilePBits, x.vals[ck[i] & kTilePMask]);
+        }
     }
     __syncthreads();   // the chunk's buffers are refilled next
     return nruns;
 }
 
 // First position of B_t*[pos + 1 .. hi) whose column is c1 or more (hi if
-// none), by binary search.
+// none, also when the range is empty), by binary search.
 __device__ __forceinline__ int tile_seg_end(const int32_t *bcol, int pos, int hi, int c1) {
     int lo = pos + 1, h = hi;
     while (lo < h) {
         const int mid = (lo + h) >> 1;
         if (__ldg(bcol + mid) < c1) lo = mid + 1; else h = mid;
     }
-    return lo;
+    return lo < hi ? lo : hi;
 }
 
 template <class P>
@@ -714,7 +773,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
     x.keyB = reinterpret_cast<uint32_t *>(sm + S::kKeyB);
     x.vals = reinterpret_cast<T *>(sm + S::kVals);
     x.lidx = reinterpret_cast<uint16_t *>(sm + S::kLidx);
-    x.cnt = reinterpret_cast<uint16_t *>(sm + S::kCnt);
+    x.cnt = reinterpret_cast<uint32_t *>(sm + S::kCnt);
     x.htop = reinterpret_cast<T *>(sm + S::kHTop);
     x.hpend = reinterpret_cast<T *>(sm + S::kHPend);
     x.hmask = reinterpret_cast<uint32_t *>(sm + S::kHMask);

@@ -1,15 +1,16 @@
 """Long rows by column tiles (option long_window).
 
-A long row of at most 2048 lists is cut into column tiles planned from the
-symbolic pass's bitmap and per-cell product histogram; every tile's products
-are sorted by column in shared memory (a stable radix sort that keeps list
-order) and Algorithm 1's merge rounds run on the sorted positions; a single
-crowded cell of more than 2048 products is taken in chunks of aligned list
-blocks, every column's chunk sums carried between them.  Rows of more lists
+A long row of at most 2048 lists is cut into column tiles of at most 2048
+products planned from the symbolic pass's bitmap and per-cell product
+histogram; every tile's products are sorted by column in shared memory (a
+stable radix sort that keeps list order) and Algorithm 1's merge rounds run
+on the sorted positions; a single crowded cell of more than 2048 products is
+taken in chunks of aligned list blocks, every column's chunk sums carried
+between them.  Rows of more lists
 keep the merge rounds in the same pass.  The result must be the merge
 rounds' bits and the oracle's Algorithm 1 in every precision.  The cases
-reach: tiles of many cells and of one cell, hot cells with runs of up to
-2048 products (many chunks), a single run that fills a tile, spans of
+reach: tiles of many cells and of one cell, hot cells of several crowded
+columns (many chunks), a single run of 2048 products, spans of
 several tiles, B wider than one bitmap window of 2^20 columns, rows past the
 2048-list limit (merge rounds instead, alone and mixed with tiled rows),
 BRMerge-Upper (the plan made in the numeric pass), batched products and a
@@ -91,14 +92,14 @@ def test_windows_are_taken():
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
 @pytest.mark.parametrize("ncols", [4096, 1 << 20])
 def test_hot_cells(mode, dtype, comp, ncols):
-    """Columns 0..3 in most of up to 2048 lists: single-cell tiles far beyond
-    one sort (runs of up to 2048 products, many chunks of aligned list
-    blocks), a cell of warm columns, cold columns spread wide; one row of 5000
-    lists keeps the merge rounds.  With 4096 columns every cell is one column
-    wide; with 2^20, 128."""
+    """Columns 0..3 in most of up to 2048 lists: with 2^20 columns (cells of
+    128) they share one cell of up to ~6500 products, taken in chunks of
+    aligned list blocks; with 4096 columns every cell is one column wide and
+    each of them a tile of up to 2048 products.  A cell of warm columns, cold
+    columns spread wide; one row of 5000 lists keeps the merge rounds."""
     k = 70000
     hot_cols = [0, 1, 2, 3] + list(range(16, 200, 3))
-    hot_p = [0.97, 0.5, 0.08, 0.03] + [0.01] * (len(hot_cols) - 4)
+    hot_p = [0.97, 0.9, 0.8, 0.5] + [0.01] * (len(hot_cols) - 4)
     B = hot_b(k, ncols, 91, hot_cols, hot_p, 3)
     A = rows_of_a([2048, 2047, 1500, 1025, 5000, 600, 1], k, 92)
     ref = oracle.alg1(A, B, prec=mode)
@@ -111,17 +112,18 @@ def test_hot_cells(mode, dtype, comp, ncols):
 
 
 def test_windows_degenerate_rows():
-    """Every list the same one column (one run of 2048 products filling a
-    tile; 2045 of them and three more lists, a hot tile), one list of 10000
-    products, two identical lists, a row of 2000 lists of which only one is
-    not empty, and a row of 2049 lists (merge rounds)."""
+    """Every list the same one column (one run of 2048 products), 1096 of
+    them and 949 lists of five columns of the same cell (a hot tile of 5841
+    products), one list of 10000 products, two identical lists, a row of
+    2000 lists of which only one is not empty, and a row of 2049 lists
+    (merge rounds)."""
     k, ncols = 6000, 300000
     one = [np.array([777])] * 2048
     wide = [np.arange(0, 300000, 30)]
     pair = [np.arange(5, 300000, 50)] * 2
-    B = csr_from_rows(one + wide + pair + [np.array([1, 2])] * 949 + [np.zeros(0, np.int64)] * 3000, ncols, 93, 1)
+    B = csr_from_rows(one + wide + pair + [np.arange(775, 780)] * 949 + [np.zeros(0, np.int64)] * 3000, ncols, 93, 1)
     assert B.rows == k
-    A = csr_from_rows([np.arange(2048), np.concatenate([np.arange(2045), [2048, 2049, 2050]]), np.array([2048]),
+    A = csr_from_rows([np.arange(2048), np.concatenate([np.arange(1096), np.arange(2051, 3000)]), np.array([2048]),
                        np.array([2049, 2050]), np.arange(2040, 2051),
                        np.concatenate([np.arange(2048, 2049), np.arange(k - 1999, k)]), np.arange(1000, 3049)],
                       k, 94, 2)
