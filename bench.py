@@ -14,9 +14,9 @@ Metric (the paper's, Section IV-A): GFLOP/s = 2 * intermediate products / s.
 
 Printed: one JSON line with the value (device-timed, all ranks), e2e (the
 same call with host buffers: A copied in from pinned host memory and all of
-C copied back every step), the roofline of the dominant kernel (the numeric
-pass of the long rows, timed live with CUDA events that the library records
-on its launch stream), clocks sampled with nvidia-smi during the timed
+C copied back every step), the roofline of the dominant kernel (the column
+tiles of the long rows' numeric pass, k_long_tile, timed live with CUDA events
+that the library records on its launch stream), clocks sampled with nvidia-smi during the timed
 region, a cpu_baseline (the CPU oracle on a bounded sample of rows, on all
 host cores and on one), and under "also" the other configurations measured in
 the same run: the Erdos-Renyi product, the FP32 and FP32+TwoSum paths of the
@@ -56,10 +56,14 @@ BLOCK_MAX_L = 1024
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture of the current source of that kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), or None when the kernel changed after the capture:
-# numeric_long -- k_rows_long<PF64> captured at R-MAT scale 16 (39.14 GB) and
-# scaled by the long rows' products to scale 20 (x 55.89); numeric_reg --
-# k_rows_perm<PF64, 32, 8> on the ER workload itself.
-TRAFFIC = {"numeric_long": 39.144e9 * 20664164109 / 369754535, "numeric_reg": 3.900762e9 + 3.183467e9}
+# numeric_tile -- k_long_tile<PF64>; numeric_reg -- k_rows_perm<PF64, 32, 8>
+# on the ER workload itself.
+TRAFFIC = {"numeric_tile": None, "numeric_reg": 3.900762e9 + 3.183467e9}
+
+# Long rows that take the column tiles by default (include/brm.h, option
+# long_window): at most this many lists and at least this many products.
+TILE_MAX_L = 2048
+TILE_MIN_NPROD = 65536
 
 
 def workload_name(scale: int) -> str:
@@ -200,6 +204,12 @@ def numeric_bytes(A, B, rows_mask, row_nnz_c, vbytes):
 def long_rows_mask(A, nprod):
     L = np.diff(A.rp.astype(np.int64))
     return (nprod > 0) & ((nprod > BLOCK_MAX_NPROD) | (L > BLOCK_MAX_L))
+
+
+def tile_rows_mask(A, nprod):
+    """The long rows of the column tiles under the default options."""
+    L = np.diff(A.rp.astype(np.int64))
+    return long_rows_mask(A, nprod) & (L <= TILE_MAX_L) & (nprod >= TILE_MIN_NPROD)
 
 
 def roofline(trace, phase, alg_bytes, traffic_key):
@@ -363,7 +373,7 @@ def run_gpu(args):
     else:
         A = I.rmat(args.scale, 16, seed=seed)
         wname = workload_name(args.scale)
-        phase = "numeric_long"
+        phase = "numeric_tile"
     vbytes = 8
     nprod = oracle.row_nprod(A, A)
     nprod_total = int(nprod.sum())
@@ -478,8 +488,8 @@ def run_gpu(args):
         return
 
     # ---- roofline of the dominant kernel ------------------------------------
-    if phase == "numeric_long":
-        mask = long_rows_mask(A, nprod)
+    if phase == "numeric_tile":
+        mask = tile_rows_mask(A, nprod)
     else:
         L = np.diff(A.rp.astype(np.int64))
         mask = (nprod > 0) & (nprod <= 1024) & (L <= 256)

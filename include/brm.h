@@ -420,8 +420,9 @@ int brm_row_split(const brm_csr *A, const brm_csr *B, int32_t parts, int64_t *bo
  * records CUDA events on its stream around each kernel phase; the elapsed
  * device times are added per phase when the call returns.  Phases, in order:
  * validate, bin, symbolic_reg, symbolic_warp, symbolic_block, symbolic_long,
- * scan, numeric_reg, numeric_warp, numeric_block, numeric_long, compact,
- * backward.  Not thread-safe across
+ * scan, numeric_reg, numeric_warp, numeric_block, numeric_long (the long
+ * rows' merge rounds), compact, backward, symbolic_tile and numeric_tile (the
+ * column tiles of the long rows, option long_window).  Not thread-safe across
  * concurrent calls from several host threads.
  *   brm_trace_enable      on != 0 enables; returns the previous setting.
  *   brm_trace_reset       zeroes the accumulated times and launch counts.

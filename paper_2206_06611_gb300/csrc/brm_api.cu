@@ -607,8 +607,6 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         PhaseScope ps(trace ? (v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg)) : -1, st);
         BRM_CUDA(launch_rows(v, b, jb, st));
     }
-    if (lp.starts.size() < 2 && !(wp && wp->on)) return BRM_OK;
-    PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
     if (wp && wp->on) {
         // the tiled long rows in one launch (two with the plan)
         RowJob jb = j;
@@ -616,8 +614,11 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         jb.count = (int32_t)((int64_t)pl.long_rows_h.size() - pl.long_split);
         jb.slot_nprod = pl.long_nprod_s + pl.long_split;
         win_job(jb, *wp, v == kIdx || !wp->planned);
+        PhaseScope ps(trace ? (v == kIdx ? kPhSymTile : kPhNumTile) : -1, st);
         BRM_CUDA(launch_rows(v, kBinLong, jb, st));
     }
+    if (lp.starts.size() < 2) return BRM_OK;
+    PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
     for (size_t bi = 0; bi + 1 < lp.starts.size(); ++bi) {
         RowJob jb = j;
         jb.rows = pl.long_rows_s + lp.starts[bi];
@@ -1436,7 +1437,8 @@ int brm_row_split(const brm_csr *A, const brm_csr *B, int32_t parts, int64_t *bo
 
 static const char *kPhaseNames[kNumPhases] = {
     "validate", "bin", "symbolic_reg", "symbolic_warp", "symbolic_block", "symbolic_long", "scan",
-    "numeric_reg", "numeric_warp", "numeric_block", "numeric_long", "compact", "backward"};
+    "numeric_reg", "numeric_warp", "numeric_block", "numeric_long", "compact", "backward", "symbolic_tile",
+    "numeric_tile"};
 
 int brm_trace_enable(int on) {
     const int was = g_trace.on ? 1 : 0;

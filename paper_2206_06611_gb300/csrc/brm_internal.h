@@ -113,7 +113,7 @@ __host__ __device__ constexpr int64_t win_span_cap(int64_t n) { return 2 * (n / 
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {
     kPhValidate = 0, kPhBin, kPhSymReg, kPhSymWarp, kPhSymBlock, kPhSymLong, kPhScan,
-    kPhNumReg, kPhNumWarp, kPhNumBlock, kPhNumLong, kPhCompact, kPhBackward, kNumPhases
+    kPhNumReg, kPhNumWarp, kPhNumBlock, kPhNumLong, kPhCompact, kPhBackward, kPhSymTile, kPhNumTile, kNumPhases
 };
 
 // Kernel launches made by the library so far (all threads).

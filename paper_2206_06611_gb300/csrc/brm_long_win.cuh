@@ -126,26 +126,23 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                 const int ncl = min(NT, ri.L - t0);
                 const int tot = lb_load_chunk<float, NT>(g, ri, t0, s_q0, s_off, nullptr);
                 for (int base = 0; base < tot; base += NT * K) {
-                    // every lane takes part (the warp's equal cells are counted
-                    // with one add); lanes past the products hold none
                     const int p0 = base + tid * K;
-                    int tl[K], q[K];
+                    if (p0 < tot) {
+                        int tl[K], q[K];
+                        lb_locate<K>(s_off, s_q0, ncl, tot, p0, tl, q);
+                        int32_t c[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) q[k] = -1;
-                    if (p0 < tot) lb_locate<K>(s_off, s_q0, ncl, tot, p0, tl, q);
-                    int32_t c[K];
+                        for (int k = 0; k < K; ++k) c[k] = q[k] >= 0 ? __ldg(ri.bcol + q[k]) : -1;
 #pragma unroll
-                    for (int k = 0; k < K; ++k) c[k] = q[k] >= 0 ? __ldg(ri.bcol + q[k]) : -1;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
-                        const bool in = q[k] >= 0 && c[k] >= 0 && u < wn;
-                        // a column already set needs no atomic (hub columns
-                        // recur in many lists)
-                        if (in && !(bm[u >> 5] & (1u << (u & 31)))) atomicOr(&bm[u >> 5], 1u << (u & 31));
-                        const int cell = in ? (int)(u >> sh) : -1;
-                        const unsigned peers = __match_any_sync(0xffffffffu, cell);
-                        if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[cell], (unsigned)__popc(peers));
+                        for (int k = 0; k < K; ++k) {
+                            const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
+                            if (q[k] >= 0 && c[k] >= 0 && u < wn) {
+                                // a column already set needs no atomic (hub
+                                // columns recur in many lists)
+                                if (!(bm[u >> 5] & (1u << (u & 31)))) atomicOr(&bm[u >> 5], 1u << (u & 31));
+                                atomicAdd(&hist[u >> sh], 1u);
+                            }
+                        }
                     }
                 }
                 g.sync();

@@ -52,13 +52,14 @@ def same(C1, C2):
 
 
 def long_trace(A, B, **kw):
-    """(symbolic_long, numeric_long) launches of one Precise call."""
+    """Launches of the long rows' symbolic and numeric passes (tiles and merge
+    rounds) in one Precise call."""
     brm.brm_trace_reset()
     was = brm.brm_trace_enable(True)
     run(A, B, **kw)
     t = brm.brm_trace_read()
     brm.brm_trace_enable(was)
-    return t["symbolic_long"][1], t["numeric_long"][1]
+    return (t["symbolic_long"][1] + t["symbolic_tile"][1], t["numeric_long"][1] + t["numeric_tile"][1])
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
