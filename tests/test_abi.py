@@ -76,7 +76,7 @@ def test_trace_api_without_gpu(lib):
     n = lib.brm_trace_read(None, None, 0)
     names = [lib.brm_trace_phase_name(i).decode() for i in range(n)]
     assert names[0] == "validate" and "numeric_reg" in names and "numeric_warp" in names
-    assert names[-2:] == ["compact", "backward"]
+    assert names[-4:] == ["compact", "backward", "symbolic_tile", "numeric_tile"]
     assert lib.brm_trace_phase_name(99) == b""
     was = lib.brm_trace_enable(1)
     assert lib.brm_trace_enable(was) == 1
