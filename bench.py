@@ -56,9 +56,10 @@ BLOCK_MAX_L = 1024
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture of the current source of that kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), or None when the kernel changed after the capture:
-# numeric_tile -- k_long_tile<PF64>; numeric_reg -- k_rows_perm<PF64, 32, 8>
-# on the ER workload itself.
-TRAFFIC = {"numeric_tile": None, "numeric_reg": 3.900762e9 + 3.183467e9}
+# numeric_tile -- k_long_tile<PF64> on the R-MAT scale 20 workload itself (a
+# one-pass capture of those two counters); numeric_reg -- k_rows_perm<PF64,
+# 32, 8> on the ER workload itself.
+TRAFFIC = {"numeric_tile": 46627292416 + 66493820928, "numeric_reg": 3.900762e9 + 3.183467e9}
 
 # Long rows that take the column tiles by default (include/brm.h, option
 # long_window): at most this many lists and at least this many products.
@@ -760,7 +761,8 @@ def run_profile(args):
         A = I.rmat(args.scale, 16) if args.workload == "rmat" else I.erdos_renyi(args.profile_n, 16)
         dA = brm.to_device(A, device="cuda:0")
         for _ in range(2):
-            C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket, long_window=args.long_window)
+            lw = {"long_window": True} if args.long_window else {}   # else the library's default
+            C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket, **lw)
             torch.cuda.synchronize()
             del C
         info = {"profile": args.workload, "n": A.rows, "long_bucket": args.long_bucket,
@@ -792,7 +794,8 @@ def main():
     ap.add_argument("--long-bucket", action="store_true",
                     help="--profile: long rows' numeric pass by column buckets (option long_bucket)")
     ap.add_argument("--long-window", action="store_true",
-                    help="--profile: long rows by column tiles (option long_window)")
+                    help="--profile: every long row of at most 2048 lists by column tiles (option long_window 2; "
+                         "by default the library's split)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
