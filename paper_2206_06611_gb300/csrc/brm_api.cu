@@ -450,6 +450,8 @@ struct WinPlan {
     int64_t *rownnz = nullptr;
     int2 *spans = nullptr;
     unsigned long long *ctr = nullptr;
+    int32_t *cur = nullptr;        // per block: cursors of rows of more than kTileSmemL lists
+    int32_t maxL = 0;
     int32_t grid = 0;
 };
 
@@ -460,10 +462,11 @@ int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKin
     if (nl == s0 || !tiles_apply(o, bcols)) return BRM_OK;
     const int64_t nt = nl - s0;
     std::vector<int64_t> base((size_t)nt + 1, 0);
-    int64_t spans = 0;
+    int64_t spans = 0, maxL = 0;
     for (int64_t s = 0; s < nt; ++s) {
         base[s + 1] = base[s] + win_cap(pl.long_nprod_h[s0 + s], bcols);
         spans += win_span_cap(pl.long_nprod_h[s0 + s]);
+        maxL = std::max<int64_t>(maxL, pl.long_L_h[s0 + s]);
     }
     wp.grid = long_win_grid(vnum == kIdx ? kF64 : vnum);
     int rc;
@@ -474,6 +477,10 @@ int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKin
     if ((rc = get(mem, wp.rownnz, (size_t)nt, "long-row lengths"))) return rc;
     if ((rc = get(mem, wp.spans, (size_t)std::max<int64_t>(spans, 1), "tile spans"))) return rc;
     if ((rc = get(mem, wp.ctr, 2, "span counters"))) return rc;
+    if (maxL > kTileSmemL && vnum != kIdx) {
+        wp.maxL = (int32_t)maxL;
+        if ((rc = get(mem, wp.cur, (size_t)wp.grid * 3 * (size_t)maxL, "list cursors"))) return rc;
+    }
     BRM_CUDA(cudaMemcpyAsync(wp.base, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice, mem.st));
     BRM_CUDA(cudaStreamSynchronize(mem.st));   // the host offsets must outlive the copy
     wp.on = true;
@@ -489,6 +496,8 @@ void win_job(RowJob &jb, const WinPlan &wp, bool plan_here) {
     jb.win_rownnz = wp.rownnz;
     jb.win_spans = wp.spans;
     jb.win_ctr = wp.ctr;
+    jb.win_cur = wp.cur;
+    jb.win_maxL = wp.maxL;
     jb.win_grid = wp.grid;
     jb.win_plan = plan_here ? 1 : 0;
 }

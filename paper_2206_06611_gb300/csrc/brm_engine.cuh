@@ -221,7 +221,8 @@ struct RowJob {
     // long rows by column tiles (brm_long_win.cuh): per long slot, where its
     // tiles start (count + 1 entries), how many it has, tiles per span, the
     // row's distinct columns; the span list and its two counters (spans
-    // written, spans taken)
+    // written, spans taken); per block of the numeric kernel, cursors for the
+    // rows of more than kTileSmemL lists (3 x win_maxL ints, or null)
     struct WinRec *win;
     const int64_t *win_base;
     int32_t *win_n;
@@ -229,6 +230,8 @@ struct RowJob {
     int64_t *win_rownnz;
     int2 *win_spans;
     unsigned long long *win_ctr;
+    int32_t *win_cur;
+    int32_t win_maxL;
     int32_t win_grid;       // persistent blocks of the numeric kernel
     int32_t win_plan;       // 1: this pass computes the plan first (symbolic pass, or Upper)
 };

@@ -74,7 +74,8 @@ __host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUn
 constexpr int kTileP = 2048;
 constexpr int kTilePBits = 11;
 constexpr int kTileThreads = 256;
-constexpr int kTileMaxL = 2048;
+constexpr int kTileMaxL = 65535;     // 16-bit list index
+constexpr int kTileSmemL = 2048;     // lists whose cursors fit shared memory (more: device memory)
 // long rows of fewer products keep the merge rounds (measured faster there)
 constexpr int64_t kTileMinNprod = 65536;
 constexpr int kWinH = 256;
@@ -84,7 +85,7 @@ constexpr int kWinCellMax = (int)(kWinBitmapCols / kWinCells);
 constexpr int64_t kWinSpanMin = 32768;
 constexpr int kWinSpanPerList = 16;
 static_assert((1 << kTilePBits) == kTileP, "a tile position fits the key's low bits");
-static_assert(kTileMaxL <= kTileP, "one column of a tile holds at most kTileMaxL products");
+static_assert(kTileSmemL <= kTileP, "a tile that fits one sort has at most kTileP segments");
 static_assert(kWinCellMax == 128, "cells are at most 128 columns wide");
 static_assert((((kWinBitmapCols - 1) << kTilePBits) | (kTileP - 1)) <= 0xffffffffLL, "key = column offset and position");
 

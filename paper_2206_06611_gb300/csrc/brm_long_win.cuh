@@ -51,7 +51,11 @@
 //   complete subtree of the merge tree, and the chunks' sums of every column
 //   are added by a tree stack per column, carried across the chunks, with
 //   the join level of two blocks bitlen(a1 2^k1 ^ a2 2^k2).
-// Limits: at most kTileMaxL lists per row (11-bit list levels), B at most
+// Lists are taken in blocks of kTileSmemL (an aligned subtree): the segment
+// search runs block by block, a hot tile is chunked block by block, and a
+// row of more than kTileSmemL lists keeps its cursors in the block's slice
+// of device memory.
+// Limits: at most kTileMaxL lists per row (16-bit list index), B at most
 // 2^24 columns; the host keeps the arena merge rounds for other long rows.
 #pragma once
 
@@ -77,16 +81,24 @@ __host__ __device__ constexpr int win_shift(int64_t wn) {
     return b > 13 ? b - 13 : 0;
 }
 
-// Levels of the tree: two lists t1 < t2 < kTileMaxL meet at level
-// bitlen(t1 ^ t2) in 1 .. 11.
-constexpr int kTileLevels = 11;
-static_assert((1 << kTileLevels) == kTileMaxL, "list levels");
+// Levels of the tree: two lists t1 < t2 <= kTileMaxL meet at level
+// bitlen(t1 ^ t2) in 1 .. 16; a block of kTileSmemL lists spans 11 of them.
+constexpr int kTileLevels = 16;
+static_assert((1 << kTileLevels) == kTileMaxL + 1, "list levels");
+constexpr int kTileChunkLevels = 11;
+static_assert((1 << kTileChunkLevels) == kTileSmemL, "a list block is an aligned subtree");
 constexpr uint32_t kWinEmpty = 0xffffffffu;   // carried state of a column that has no sum yet
 constexpr uint32_t kTilePMask = (1u << kTilePBits) - 1u;
 constexpr uint16_t kTileRet = 0x8000u;         // a retired position of the merge rounds
 static_assert(kTileP < kTileRet, "positions fit 15 bits");
 constexpr int kTileNW = kTileThreads / 32;
+// 5-bit fields of the merge rounds' meeting levels, one per owned position
+constexpr uint64_t kTileField1 = 0x0000000842108421ull;   // 1 in each of 8 fields
+constexpr uint64_t kTileFieldLo = kTileField1 * 15u;        // the low 4 bits of each field
+constexpr uint64_t kTileFieldHi = kTileField1 * 16u;        // the top bit of each field
+constexpr uint64_t kTileNoMeetAll = kTileField1 * 31u;      // every field 31: no meeting
 constexpr int kTileQ = kTileP / kTileThreads;   // sorted positions per thread
+static_assert(kTileQ == 8, "eight 5-bit level fields per thread");
 static_assert(kTileThreads >= 256 && kTileThreads % 256 == 0, "a radix digit per thread of the first 256");
 constexpr int kTileWords = kTileP / 32;            // words of a position bitmap
 static_assert(kTileWords % 32 == 0, "whole words per lane");
@@ -337,13 +349,13 @@ __device__ __forceinline__ int tile_bitlen(uint32_t x) { return 32 - __clz((int)
 template <class P>
 struct TileSmem {
     using T = typename P::T;
-    static constexpr size_t kCpos = 0;                                              // int32[kTileMaxL]
-    static constexpr size_t kCcol = kCpos + 4 * kTileMaxL;                          // int32[kTileMaxL]
-    static constexpr size_t kCend = kCcol + 4 * kTileMaxL;                          // int32[kTileMaxL]
-    static constexpr size_t kSegQ = kCend + 4 * kTileMaxL;                          // int32[kTileMaxL]
-    static constexpr size_t kSegOff = kSegQ + 4 * kTileMaxL;                        // int32[kTileMaxL + 1]
-    static constexpr size_t kSegT = align_up(kSegOff + 4 * (kTileMaxL + 1), 16);    // uint16[kTileMaxL]
-    static constexpr size_t kBits = align_up(kSegT + 2 * kTileMaxL, 16);            // uint32[kTileP / 32]
+    static constexpr size_t kCpos = 0;                                              // int32[kTileSmemL]
+    static constexpr size_t kCcol = kCpos + 4 * kTileSmemL;                          // int32[kTileSmemL]
+    static constexpr size_t kCend = kCcol + 4 * kTileSmemL;                          // int32[kTileSmemL]
+    static constexpr size_t kSegQ = kCend + 4 * kTileSmemL;                          // int32[kTileSmemL]
+    static constexpr size_t kSegOff = kSegQ + 4 * kTileSmemL;                        // int32[kTileSmemL + 1]
+    static constexpr size_t kSegT = align_up(kSegOff + 4 * (kTileSmemL + 1), 16);    // uint16[kTileSmemL]
+    static constexpr size_t kBits = align_up(kSegT + 2 * kTileSmemL, 16);            // uint32[kTileP / 32]
     static constexpr size_t kWpre = kBits + 4 * (kTileP / 32);                      // int32[kTileP / 32]
     static constexpr size_t kKeyA = kWpre + 4 * (kTileP / 32);                      // uint32[kTileP]
     static constexpr size_t kKeyB = kKeyA + 4 * kTileP;                             // uint32[kTileP]
@@ -355,7 +367,7 @@ struct TileSmem {
     static constexpr size_t kHMask = kHPend + sizeof(T) * kTileLevels * kWinCellMax;   // uint32[kWinCellMax]
     static constexpr size_t kHLast = kHMask + 4 * kWinCellMax;                      // int32[kWinCellMax]
     static constexpr size_t kBytes = align_up(kHLast + 4 * kWinCellMax, 16);
-    static_assert(kTileP >= kTileMaxL, "the search scratch fits a key buffer");
+    static_assert(kTileP >= kTileSmemL, "the search scratch of a list block fits a key buffer");
 };
 
 // Exclusive prefix sums of (a, b) over the block, totals in (ta, tb).
@@ -639,7 +651,7 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     // meet in round bitlen(t_left ^ t_right), and nothing changes that round
     // before it: the right one can be retired only by its left neighbour, and
     // the left one gets a new neighbour only by taking this one.  Each
-    // position keeps that level (15: no next sum in its column) and
+    // position keeps that level (31: no next sum in its column) and
     // round h handles just the positions whose level is h; after taking its
     // neighbour, a sum meets the next one in a later round (three live sums
     // of one column cannot share t >> h).  The leftmost sum of a column is
@@ -649,7 +661,7 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     uint32_t *rs = x.bits;                                        // run starts, one bit per position
     int32_t *rpre = x.wpre;                                       // run starts before every word
     // thread tid owns positions tid + kTileThreads * i, with their meeting
-    // levels in the nibbles of lv; warp w's lanes cover the word i * kTileNW +
+    // levels in the 5-bit fields of lv; warp w's lanes cover the word i * kTileNW +
     // w of the run-start bitmap
     uint32_t ck[kTileQ];   // the owned sorted keys
 #pragma unroll
@@ -663,7 +675,7 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
         }
     }
     __syncthreads();
-    uint32_t lv = 0xffffffffu;
+    uint64_t lv = kTileNoMeetAll;
 #pragma unroll
     for (int i = 0; i < kTileQ; ++i) {
         const int s = tid + kTileThreads * i;
@@ -671,8 +683,8 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
         if (s < n) {
             start = s == 0 || (K[s - 1] >> kTilePBits) != (ck[i] >> kTilePBits);
             if (s + 1 < n && (K[s + 1] >> kTilePBits) == (ck[i] >> kTilePBits)) {
-                const uint32_t m = (uint32_t)tile_bitlen((uint32_t)(st[s] ^ st[s + 1]));
-                lv = (lv & ~(15u << (4 * i))) | (m << (4 * i));
+                const uint64_t m = (uint64_t)tile_bitlen((uint32_t)(st[s] ^ st[s + 1]));
+                lv = (lv & ~(31ull << (5 * i))) | (m << (5 * i));
             }
         }
         const unsigned b = __ballot_sync(kFull, start);
@@ -680,18 +692,18 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     }
     __syncthreads();
     if (wid == 0) tile_word_prefix(rs, rpre, kTileWords);
-    for (int h = 1; h <= 15 && __syncthreads_or(lv != 0xffffffffu); ++h) {
-        // owned positions whose level is h: the zero nibbles of lv ^ h...h
-        const uint32_t e = lv ^ (0x11111111u * (uint32_t)h);
-        uint32_t z = ~(((e & 0x77777777u) + 0x77777777u) | e) & 0x88888888u;
+    for (int h = 1; h <= kTileLevels && __syncthreads_or(lv != kTileNoMeetAll); ++h) {
+        // owned positions whose level is h: the zero fields of lv ^ h...h
+        const uint64_t e = lv ^ (kTileField1 * (uint64_t)h);
+        uint64_t z = ~(((e & kTileFieldLo) + kTileFieldLo) | e) & kTileFieldHi;
         while (z) {
-            const int bit = __ffs(z) - 1;
+            const int bit = __ffsll((long long)z) - 1;
             z &= z - 1u;
-            const int i = bit >> 2;
+            const int i = bit / 5;
             const int s = tid + kTileThreads * i;
             const int j = nxt[s];
             if (j & kTileRet) {   // retired by its left neighbour: it meets nothing any more
-                lv |= 15u << (4 * i);
+                lv |= 31ull << (5 * i);
                 continue;
             }
             const uint32_t kss = K[s], kjj = K[j];
@@ -700,10 +712,10 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
             const int k = nxt[j];
             nxt[s] = (uint16_t)k;
             nxt[j] = (uint16_t)(k | kTileRet);
-            uint32_t m = 15u;
+            uint64_t m = 31u;
             if (k < n && (K[k] >> kTilePBits) == (kss >> kTilePBits))
-                m = (uint32_t)tile_bitlen((uint32_t)(st[s] ^ st[k]));
-            lv = (lv & ~(15u << (4 * i))) | (m << (4 * i));
+                m = (uint64_t)tile_bitlen((uint32_t)(st[s] ^ st[k]));
+            lv = (lv & ~(31ull << (5 * i))) | (m << (5 * i));
         }
     }
     __syncthreads();
@@ -746,9 +758,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
     __shared__ int s_chunk[4];
     __shared__ unsigned long long s_span;
     const int tid = threadIdx.x;
-    int32_t *cpos = reinterpret_cast<int32_t *>(sm + S::kCpos);
-    int32_t *ccol = reinterpret_cast<int32_t *>(sm + S::kCcol);
-    int32_t *cend = reinterpret_cast<int32_t *>(sm + S::kCend);
+    int32_t *cpos_s = reinterpret_cast<int32_t *>(sm + S::kCpos);
+    int32_t *ccol_s = reinterpret_cast<int32_t *>(sm + S::kCcol);
+    int32_t *cend_s = reinterpret_cast<int32_t *>(sm + S::kCend);
     int32_t *segq = reinterpret_cast<int32_t *>(sm + S::kSegQ);
     int32_t *segoff = reinterpret_cast<int32_t *>(sm + S::kSegOff);
     uint16_t *segt = reinterpret_cast<uint16_t *>(sm + S::kSegT);
@@ -798,13 +810,22 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
         const int64_t slot = j.out_rp[row + 1] - obase;
         if (sp.y == 0 && tid == 0 && (rownnz > slot || (j.exact && rownnz != slot))) atomicOr(j.err, 1u);
         if (w0 >= w1) continue;
-        if (L > kTileMaxL) {
+        if (L > kTileMaxL || (L > kTileSmemL && (j.win_cur == nullptr || L > j.win_maxL))) {
             if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: the host gives such rows the merge rounds
             continue;
         }
         x.aval = ri.aval;
         x.bcol = ri.bcol;
         x.bval = ri.bval;
+        // cursors: in shared memory, or for rows of more lists in this block's
+        // slice of device memory
+        int32_t *cpos = cpos_s, *ccol = ccol_s, *cend = cend_s;
+        if (L > kTileSmemL) {
+            int32_t *cg = j.win_cur + (size_t)blockIdx.x * 3 * (size_t)j.win_maxL;
+            cpos = cg;
+            ccol = cg + j.win_maxL;
+            cend = cg + 2 * (size_t)j.win_maxL;
+        }
 
         // cursors at the span's first column
         const int cstart = wr[w0].c0;
@@ -823,8 +844,6 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
         }
         __syncthreads();
 
-        const int J = (L + NT - 1) / NT;
-        const int t0 = min(L, tid * J), t1 = min(L, t0 + J);
         for (int w = w0; w < w1; ++w) {
             const WinRec rec = wr[w];
             if (rec.np == 0) continue;
@@ -835,121 +854,142 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
             x.oval = static_cast<Out *>(j.out_val) + obase + rec.off;
             x.expect = (w + 1 < nwin ? wr[w + 1].off : rownnz) - rec.off;
             if (rec.off + x.expect > slot) x.expect = rec.off < slot ? slot - rec.off : 0;   // flagged above
-
-            // 1. every list's segment below c1, numbered in list order; the
-            // next four columns of up to four lists are loaded at once
-            int ns = 0, np = 0;
-            for (int tq = t0; tq < t1; tq += 4) {
-                int cu[4][4], pos[4], hi[4];
+            const bool hot = rec.np > kTileP;
+            if (hot)
+                for (int c = tid; c < kWinCellMax; c += NT) x.hmask[c] = kWinEmpty;
+            // the lists in blocks of kTileSmemL: a tile that fits one sort
+            // gathers every block's segments into one table (at most kTileP of
+            // them: a segment holds a product), a hot tile takes each block's
+            // segments in chunks before the next block
+            int tns = 0, tnp = 0;
+            for (int lb = 0; lb < L; lb += kTileSmemL) {
+                const int lbe = min(L, lb + kTileSmemL);
+                const int J = (lbe - lb + NT - 1) / NT;
+                const int t0 = min(lbe, lb + tid * J), t1 = min(lbe, t0 + J);
+                // 1. every list's segment below c1, numbered in list order; the
+                // next four columns of up to four lists are loaded at once
+                int ns = 0, np = 0;
+                for (int tq = t0; tq < t1; tq += 4) {
+                    int cu[4][4], pos[4], hi[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = tq + u;
-                    pos[u] = -1;
-                    hi[u] = 0;
-                    if (t < t1) {
-                        const int col = ccol[t];
-                        if (col < c1) {
-                            pos[u] = cpos[t];
-                            hi[u] = (int)min((int64_t)cend[t], (int64_t)pos[u] + ((int64_t)c1 - col));
-                        }
-                    }
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        cu[u][v] = pos[u] >= 0 && pos[u] + 1 + v < hi[u] ? __ldg(ri.bcol + pos[u] + 1 + v) : INT_MAX;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = tq + u;
-                    if (t < t1) {
-                        int len = 0;
-                        if (pos[u] >= 0) {
-                            const int p = pos[u], end = cend[t];
-                            int e = -1, ncol = INT_MAX;
-#pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                if (e < 0 && p + 1 + v < hi[u] && cu[u][v] >= c1) {
-                                    e = p + 1 + v;
-                                    ncol = cu[u][v];
-                                }
-                            if (e < 0) {
-                                e = tile_seg_end(ri.bcol, p + 4, hi[u], c1);
-                                ncol = e < end ? __ldg(ri.bcol + e) : INT_MAX;
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = tq + u;
+                        pos[u] = -1;
+                        hi[u] = 0;
+                        if (t < t1) {
+                            const int col = ccol[t];
+                            if (col < c1) {
+                                pos[u] = cpos[t];
+                                hi[u] = (int)min((int64_t)cend[t], (int64_t)pos[u] + ((int64_t)c1 - col));
                             }
-                            len = e - p;
-                            cpos[t] = e;
-                            ccol[t] = ncol;
-                            tpos[t] = p;
                         }
-                        tlen[t] = len;
-                        ns += len > 0 ? 1 : 0;
-                        np += len;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            cu[u][v] = pos[u] >= 0 && pos[u] + 1 + v < hi[u] ? __ldg(ri.bcol + pos[u] + 1 + v)
+                                                                            : INT_MAX;
                     }
-                }
-            }
-            int tns, tnp;
-            const int2 ex = tile_scan2(ns, np, tns, tnp, ws2);
-            {
-                int si = ex.x, po = ex.y;
-                for (int t = t0; t < t1; ++t) {
-                    const int len = tlen[t];
-                    if (len > 0) {
-                        segq[si] = tpos[t];
-                        segoff[si] = po;
-                        segt[si] = (uint16_t)t;
-                        ++si;
-                        po += len;
-                    }
-                }
-            }
-            if (tid == 0) {
-                segoff[tns] = tnp;
-                if (tnp != rec.np) atomicOr(j.err, 1u);
-            }
-            __syncthreads();
-            if (tnp == 0) continue;
-
-            if (tnp <= kTileP) {
-                const int nout = tile_chunk<P>(x, 0, tns, 0, tnp, false, 0);
-                if (tid == 0 && nout != x.expect) atomicOr(j.err, 1u);
-                continue;
-            }
-            // 2. a hot tile: chunks of aligned list blocks, every column's
-            // chunk sums added by its carried stack
-            for (int c = tid; c < kWinCellMax; c += NT) x.hmask[c] = kWinEmpty;
-            int cur = 0;
-            while (cur < L) {
-                if (tid == 0) {
-                    // first segment of a list >= t
-                    auto seg_at = [&](int t) {
-                        int lo = 0, hi = tns;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if ((int)segt[mid] < t) lo = mid + 1; else hi = mid;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = tq + u;
+                        if (t < t1) {
+                            int len = 0;
+                            if (pos[u] >= 0) {
+                                const int p = pos[u], end = cend[t];
+                                int e = -1, ncol = INT_MAX;
+#pragma unroll
+                                for (int v = 0; v < 4; ++v)
+                                    if (e < 0 && p + 1 + v < hi[u] && cu[u][v] >= c1) {
+                                        e = p + 1 + v;
+                                        ncol = cu[u][v];
+                                    }
+                                if (e < 0) {
+                                    e = tile_seg_end(ri.bcol, p + 4, hi[u], c1);
+                                    ncol = e < end ? __ldg(ri.bcol + e) : INT_MAX;
+                                }
+                                len = e - p;
+                                cpos[t] = e;
+                                ccol[t] = ncol;
+                                tpos[t - lb] = p;
+                            }
+                            tlen[t - lb] = len;
+                            ns += len > 0 ? 1 : 0;
+                            np += len;
                         }
-                        return lo;
-                    };
-                    int k = cur == 0 ? kTileLevels : min(__ffs(cur) - 1, kTileLevels);
-                    const int sa = seg_at(cur);
-                    int sb = sa;
-                    for (;; --k) {
-                        sb = seg_at(min(L, cur + (1 << k)));
-                        if (segoff[sb] - segoff[sa] <= kTileP || k == 0) break;
                     }
-                    s_chunk[0] = sa;
-                    s_chunk[1] = sb;
-                    s_chunk[2] = min(L, cur + (1 << k));
-                    s_chunk[3] = cur;
                 }
+                int bns, bnp;
+                const int2 ex = tile_scan2(ns, np, bns, bnp, ws2);
+                const int sbase = hot ? 0 : tns, pbase = hot ? 0 : tnp;
+                if (sbase + bns > kTileSmemL) {
+                    // cannot happen: the plan's count bounds the segments of a tile that fits one sort
+                    if (tid == 0) atomicOr(j.err, 1u);
+                    tns = -1;
+                    break;
+                }
+                {
+                    int si = sbase + ex.x, po = pbase + ex.y;
+                    for (int t = t0; t < t1; ++t) {
+                        const int len = tlen[t - lb];
+                        if (len > 0) {
+                            segq[si] = tpos[t - lb];
+                            segoff[si] = po;
+                            segt[si] = (uint16_t)t;
+                            ++si;
+                            po += len;
+                        }
+                    }
+                }
+                tns = sbase + bns;
+                tnp += bnp;
+                if (tid == 0) segoff[tns] = hot ? bnp : tnp;
                 __syncthreads();
-                const int sa = s_chunk[0], sb = s_chunk[1], nxt = s_chunk[2], tb = s_chunk[3];
-                const int pos0 = segoff[sa], n = segoff[sb] - pos0;
-                __syncthreads();   // s_chunk is rewritten next
-                if (n > kTileP) {
-                    if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: one list holds at most one cell
-                } else if (n > 0) {
-                    tile_chunk<P>(x, sa, sb, pos0, n, true, tb);
+                if (!hot || bnp == 0) continue;
+                // 2. a hot tile: this block's lists in chunks of aligned list
+                // blocks, every column's chunk sums added by its carried stack
+                int cur = lb;
+                while (cur < lbe) {
+                    if (tid == 0) {
+                        // first segment of a list >= t
+                        auto seg_at = [&](int t) {
+                            int lo = 0, hi = tns;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if ((int)segt[mid] < t) lo = mid + 1; else hi = mid;
+                            }
+                            return lo;
+                        };
+                        int k = cur == lb ? kTileChunkLevels : min(__ffs(cur) - 1, kTileChunkLevels);
+                        const int sa = seg_at(cur);
+                        int sb = sa;
+                        for (;; --k) {
+                            sb = seg_at(min(lbe, cur + (1 << k)));
+                            if (segoff[sb] - segoff[sa] <= kTileP || k == 0) break;
+                        }
+                        s_chunk[0] = sa;
+                        s_chunk[1] = sb;
+                        s_chunk[2] = min(lbe, cur + (1 << k));
+                        s_chunk[3] = cur;
+                    }
+                    __syncthreads();
+                    const int sa = s_chunk[0], sb = s_chunk[1], nxt = s_chunk[2], tb = s_chunk[3];
+                    const int pos0 = segoff[sa], n = segoff[sb] - pos0;
+                    __syncthreads();   // s_chunk is rewritten next
+                    if (n > kTileP) {
+                        if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: one list holds at most one cell
+                    } else if (n > 0) {
+                        tile_chunk<P>(x, sa, sb, pos0, n, true, tb);
+                    }
+                    cur = nxt;
                 }
-                cur = nxt;
+            }
+            if (tns < 0) continue;
+            if (tid == 0 && tnp != rec.np) atomicOr(j.err, 1u);
+            if (!hot) {
+                if (tnp > 0) {
+                    const int nout = tile_chunk<P>(x, 0, tns, 0, tnp, false, 0);
+                    if (tid == 0 && nout != x.expect) atomicOr(j.err, 1u);
+                }
+                continue;
             }
             // the columns of the cell in order
             __syncthreads();
