@@ -1,20 +1,21 @@
 """Long rows by column tiles (option long_window).
 
-A long row of at most 2048 lists is cut into column tiles of at most 2048
+A long row of at most 65535 lists is cut into column tiles of at most 2048
 products planned from the symbolic pass's bitmap and per-cell product
 histogram; every tile's products are sorted by column in shared memory (a
 stable radix sort that keeps list order) and Algorithm 1's merge rounds run
 on the sorted positions; a single crowded cell of more than 2048 products is
 taken in chunks of aligned list blocks, every column's chunk sums carried
-between them.  Rows of more lists
-keep the merge rounds in the same pass.  The result must be the merge
-rounds' bits and the oracle's Algorithm 1 in every precision.  The cases
-reach: tiles of many cells and of one cell, hot cells of several crowded
-columns (many chunks), a single run of 2048 products, spans of
-several tiles, B wider than one bitmap window of 2^20 columns, rows past the
-2048-list limit (merge rounds instead, alone and mixed with tiled rows),
-BRMerge-Upper (the plan made in the numeric pass), batched products and a
-prepared batch replayed from a CUDA graph.
+between them.  Lists are searched in blocks of 2048 (rows of more lists keep
+their cursors in device memory).  Rows of more than 65535 lists keep the
+merge rounds in the same pass.  The result must be the merge rounds' bits and
+the oracle's Algorithm 1 in every precision.  The cases reach: tiles of many
+cells and of one cell, hot cells of several crowded columns (many chunks,
+several list blocks), a single run of 2048 products, rows of up to 20000
+lists, spans of several tiles, B wider than one bitmap window of 2^20
+columns, rows past the 65535-list limit (merge rounds instead, alone and
+mixed with tiled rows), BRMerge-Upper (the plan made in the numeric pass),
+batched products and a prepared batch replayed from a CUDA graph.
 """
 import numpy as np
 import pytest
@@ -93,16 +94,16 @@ def test_windows_are_taken():
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
 @pytest.mark.parametrize("ncols", [4096, 1 << 20])
 def test_hot_cells(mode, dtype, comp, ncols):
-    """Columns 0..3 in most of up to 2048 lists: with 2^20 columns (cells of
-    128) they share one cell of up to ~6500 products, taken in chunks of
-    aligned list blocks; with 4096 columns every cell is one column wide and
-    each of them a tile of up to 2048 products.  A cell of warm columns, cold
-    columns spread wide; one row of 5000 lists keeps the merge rounds."""
+    """Columns 0..3 in most of up to 20000 lists: with 2^20 columns (cells of
+    128) they share one cell of up to ~63000 products, taken in chunks of
+    aligned list blocks, block after block of 2048 lists; with 4096 columns
+    every cell is one column wide, a tile of up to 2048 products or, past 2048
+    lists, a hot one.  A cell of warm columns, cold columns spread wide."""
     k = 70000
     hot_cols = [0, 1, 2, 3] + list(range(16, 200, 3))
     hot_p = [0.97, 0.9, 0.8, 0.5] + [0.01] * (len(hot_cols) - 4)
     B = hot_b(k, ncols, 91, hot_cols, hot_p, 3)
-    A = rows_of_a([2048, 2047, 1500, 1025, 5000, 600, 1], k, 92)
+    A = rows_of_a([20000, 5000, 2048, 2047, 1025, 600, 1], k, 92)
     ref = oracle.alg1(A, B, prec=mode)
     C = run(A, B, "precise", dtype, comp)
     assert_rows_exact(C, ref)
@@ -116,8 +117,8 @@ def test_windows_degenerate_rows():
     """Every list the same one column (one run of 2048 products), 1096 of
     them and 949 lists of five columns of the same cell (a hot tile of 5841
     products), one list of 10000 products, two identical lists, a row of
-    2000 lists of which only one is not empty, and a row of 2049 lists
-    (merge rounds)."""
+    2000 lists of which only one is not empty, and a row of 2049 lists (two
+    list blocks)."""
     k, ncols = 6000, 300000
     one = [np.array([777])] * 2048
     wide = [np.arange(0, 300000, 30)]
@@ -150,7 +151,7 @@ def test_windows_wide_B_several_bitmap_windows():
 
 
 def test_windows_list_limit_uses_merge_rounds():
-    """Rows of more than 2048 lists keep the merge rounds: alone (one
+    """Rows of more than 65535 lists keep the merge rounds: alone (one
     symbolic launch, the column bitmap), and mixed with tiled rows in the
     same passes (the plan and the bitmap, the tiles and the rounds)."""
     k, ncols = 70000, 50000
@@ -159,7 +160,7 @@ def test_windows_list_limit_uses_merge_rounds():
     assert_rows_exact(run(A, B), oracle.alg1(A, B))
     sym, num = long_trace(A, B)
     assert sym == 1 and num >= 1
-    A2 = rows_of_a([2049, 2048, 4000, 1500, 300], k, 108)
+    A2 = rows_of_a([70000, 2049, 2048, 4000, 1500, 300], k, 108)
     ref = oracle.alg1(A2, B)
     C = run(A2, B)
     assert_rows_exact(C, ref)
