@@ -156,7 +156,7 @@ def test_windows_list_limit_uses_merge_rounds():
     same passes (the plan and the bitmap, the tiles and the rounds)."""
     k, ncols = 70000, 50000
     B = hot_b(k, ncols, 97, [10, 11], [0.3, 0.3], 2)
-    A = rows_of_a([70000, 5000, 10], k, 98)
+    A = rows_of_a([70000, 69999, 10], k, 98)
     assert_rows_exact(run(A, B), oracle.alg1(A, B))
     sym, num = long_trace(A, B)
     assert sym == 1 and num >= 1
