@@ -170,11 +170,12 @@ typedef struct {
  *                  products sorted by column in shared memory and summed by
  *                  Algorithm 1's merge rounds on the sorted positions, one
  *                  thread block per tile (the same values as the merge rounds
- *                  in the arena); other long rows take the arena merge rounds
- *                  in the same pass.  2: every long row of at most 2048 lists
- *                  takes the tiles.  0: every long row takes the arena merge
- *                  rounds.  BRMerge-Upper in row chunks always takes the
- *                  arena merge rounds.
+ *                  in the arena); the other long rows take the arena merge
+ *                  rounds, launched first, with the tiles running beside them
+ *                  on a second stream of the library's.  2: every long row of
+ *                  at most 65535 lists takes the tiles.  0: every long row
+ *                  takes the arena merge rounds.  BRMerge-Upper in row chunks
+ *                  always takes the arena merge rounds.
  *   upper_chunk_bytes  BRMerge-Upper: the largest C_bar (nprod * (4 +
  *                  sizeof value) bytes) processed at once; a larger product
  *                  is processed in row chunks of at most this size, each
