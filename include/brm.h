@@ -171,8 +171,7 @@ typedef struct {
  *                  Algorithm 1's merge rounds on the sorted positions, one
  *                  thread block per tile (the same values as the merge rounds
  *                  in the arena); the other long rows take the arena merge
- *                  rounds, launched first, with the tiles running beside them
- *                  on a second stream of the library's.  2: every long row of
+ *                  rounds in the same pass.  2: every long row of
  *                  at most 65535 lists takes the tiles.  0: every long row
  *                  takes the arena merge rounds.  BRMerge-Upper in row chunks
  *                  always takes the arena merge rounds.

@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <unordered_map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -606,41 +605,6 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
     return BRM_OK;
 }
 
-// The library's second stream on the current device (created once, kept for
-// the life of the process; null if it cannot be created).
-cudaStream_t side_stream() {
-    static std::mutex mu;
-    static std::unordered_map<int, cudaStream_t> streams;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = streams.find(dev);
-    if (it != streams.end()) return it->second;
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    streams[dev] = s;
-    return s;
-}
-
-// Two events that fork a second stream from a first and join it back.
-struct EventPair {
-    cudaEvent_t fork = nullptr, join = nullptr;
-    bool create() {
-        return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
-    }
-    ~EventPair() {
-        if (fork) cudaEventDestroy(fork);
-        if (join) cudaEventDestroy(join);
-    }
-};
-
 // Kernel launches of one pass over every bin (no host synchronisation, no
 // allocation: a numeric pass of a prepared plan can be captured in a graph).
 int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cudaStream_t st, bool trace,
@@ -654,64 +618,40 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         PhaseScope ps(trace ? (v == kIdx ? ph : ph + (kPhNumReg - kPhSymReg)) : -1, st);
         BRM_CUDA(launch_rows(v, b, jb, st));
     }
-    const bool tiles = wp && wp->on, rounds = lp.starts.size() >= 2;
-    // With both kinds of long rows, the merge rounds go first (their largest
-    // rows start earliest; one row is one block's work) and the tiles run
-    // beside them on the library's second stream, filling the SMs the rounds
-    // leave; the caller's stream waits for both.  Not while the stream is
-    // being captured into a graph.
-    EventPair ev;
-    cudaStream_t ts = st;
-    if (tiles && rounds) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
-        cudaStream_t s2 = nullptr;
-        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
-            (s2 = side_stream()) != nullptr && ev.create() && cudaEventRecord(ev.fork, st) == cudaSuccess)
-            ts = s2;
-        cudaGetLastError();
-    }
-    if (rounds) {
-        PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
-        for (size_t bi = 0; bi + 1 < lp.starts.size(); ++bi) {
-            RowJob jb = j;
-            jb.rows = pl.long_rows_s + lp.starts[bi];
-            jb.count = (int32_t)(lp.starts[bi + 1] - lp.starts[bi]);
-            jb.long_bucket = lp.bucket ? 1 : 0;
-            jb.arena = lp.arena;
-            jb.arena_off = lp.off_d + lp.starts[bi];
-            if (bi < lp.work_off.size()) {
-                char *w = lp.arena + lp.work_off[bi];
-                const size_t wb = align_up((size_t)lp.work_cap[bi] * kLbWorkBytes, 256);
-                jb.lb_work = w;
-                jb.lb_ctr = reinterpret_cast<int32_t *>(w + wb);
-                jb.lb_slots = w + wb + 256;
-                jb.lb_cap = lp.work_cap[bi];
-            }
-            jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
-            if (lp.grid > 0) {
-                jb.long_grid = lp.grid;
-                jb.long_ctr = lp.ctr;
-                BRM_CUDA(cudaMemsetAsync(lp.ctr, 0, sizeof(int32_t), st));
-            }
-            BRM_CUDA(launch_rows(v, kBinLong, jb, st));
-        }
-    }
-    if (tiles) {
+    if (wp && wp->on) {
         // the tiled long rows in one launch (two with the plan)
-        if (ts != st) BRM_CUDA(cudaStreamWaitEvent(ts, ev.fork, 0));
         RowJob jb = j;
         jb.rows = pl.long_rows_s + pl.long_split;
         jb.count = (int32_t)((int64_t)pl.long_rows_h.size() - pl.long_split);
         jb.slot_nprod = pl.long_nprod_s + pl.long_split;
         win_job(jb, *wp, v == kIdx || !wp->planned);
-        {
-            PhaseScope ps(trace ? (v == kIdx ? kPhSymTile : kPhNumTile) : -1, ts);
-            BRM_CUDA(launch_rows(v, kBinLong, jb, ts));
+        PhaseScope ps(trace ? (v == kIdx ? kPhSymTile : kPhNumTile) : -1, st);
+        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
+    }
+    if (lp.starts.size() < 2) return BRM_OK;
+    PhaseScope ps(trace ? (v == kIdx ? kPhSymLong : kPhNumLong) : -1, st);
+    for (size_t bi = 0; bi + 1 < lp.starts.size(); ++bi) {
+        RowJob jb = j;
+        jb.rows = pl.long_rows_s + lp.starts[bi];
+        jb.count = (int32_t)(lp.starts[bi + 1] - lp.starts[bi]);
+        jb.long_bucket = lp.bucket ? 1 : 0;
+        jb.arena = lp.arena;
+        jb.arena_off = lp.off_d + lp.starts[bi];
+        if (bi < lp.work_off.size()) {
+            char *w = lp.arena + lp.work_off[bi];
+            const size_t wb = align_up((size_t)lp.work_cap[bi] * kLbWorkBytes, 256);
+            jb.lb_work = w;
+            jb.lb_ctr = reinterpret_cast<int32_t *>(w + wb);
+            jb.lb_slots = w + wb + 256;
+            jb.lb_cap = lp.work_cap[bi];
         }
-        if (ts != st) {
-            BRM_CUDA(cudaEventRecord(ev.join, ts));
-            BRM_CUDA(cudaStreamWaitEvent(st, ev.join, 0));
+        jb.slot_nprod = pl.long_nprod_s + lp.starts[bi];
+        if (lp.grid > 0) {
+            jb.long_grid = lp.grid;
+            jb.long_ctr = lp.ctr;
+            BRM_CUDA(cudaMemsetAsync(lp.ctr, 0, sizeof(int32_t), st));
         }
+        BRM_CUDA(launch_rows(v, kBinLong, jb, st));
     }
     return BRM_OK;
 }
