@@ -145,9 +145,6 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                         int32_t c[K];
 #pragma unroll
                         for (int k = 0; k < K; ++k) c[k] = q[k] >= 0 ? __ldg(ri.bcol + q[k]) : -1;
-                        // the thread's products come mostly from one list, in
-                        // column order: equal cells in a row make one add
-                        uint32_t cell = 0xffffffffu, run = 0;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             const uint32_t u = (uint32_t)((int64_t)c[k] - w0);
@@ -155,15 +152,9 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                                 // a column already set needs no atomic (hub
                                 // columns recur in many lists)
                                 if (!(bm[u >> 5] & (1u << (u & 31)))) atomicOr(&bm[u >> 5], 1u << (u & 31));
-                                if ((u >> sh) != cell) {
-                                    if (run) atomicAdd(&hist[cell], run);
-                                    cell = u >> sh;
-                                    run = 0;
-                                }
-                                ++run;
+                                atomicAdd(&hist[u >> sh], 1u);
                             }
                         }
-                        if (run) atomicAdd(&hist[cell], run);
                     }
                 }
                 g.sync();
@@ -704,25 +695,25 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     for (int h = 1; h <= kTileLevels && __syncthreads_or(lv != kTileNoMeetAll); ++h) {
         // owned positions whose level is h: the zero fields of lv ^ h...h
         const uint64_t e = lv ^ (kTileField1 * (uint64_t)h);
-        const uint64_t z = ~(((e & kTileFieldLo) + kTileFieldLo) | e) & kTileFieldHi;
-        if (z == 0u) continue;
-#pragma unroll
-        for (int i = 0; i < kTileQ; ++i) {
-            if (!((z >> (5 * i + 4)) & 1u)) continue;
+        uint64_t z = ~(((e & kTileFieldLo) + kTileFieldLo) | e) & kTileFieldHi;
+        while (z) {
+            const int bit = __ffsll((long long)z) - 1;
+            z &= z - 1u;
+            const int i = bit / 5;
             const int s = tid + kTileThreads * i;
             const int j = nxt[s];
             if (j & kTileRet) {   // retired by its left neighbour: it meets nothing any more
                 lv |= 31ull << (5 * i);
                 continue;
             }
-            const uint32_t kjj = K[j];
-            const int ps = (int)(ck[i] & kTilePMask), pj = (int)(kjj & kTilePMask);
+            const uint32_t kss = K[s], kjj = K[j];
+            const int ps = (int)(kss & kTilePMask), pj = (int)(kjj & kTilePMask);
             x.vals[ps] = P::add(x.vals[ps], x.vals[pj]);
             const int k = nxt[j];
             nxt[s] = (uint16_t)k;
             nxt[j] = (uint16_t)(k | kTileRet);
             uint64_t m = 31u;
-            if (k < n && (K[k] >> kTilePBits) == (ck[i] >> kTilePBits))
+            if (k < n && (K[k] >> kTilePBits) == (kss >> kTilePBits))
                 m = (uint64_t)tile_bitlen((uint32_t)(st[s] ^ st[k]));
             lv = (lv & ~(31ull << (5 * i))) | (m << (5 * i));
         }
