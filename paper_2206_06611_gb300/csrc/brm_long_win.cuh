@@ -696,63 +696,26 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
         // owned positions whose level is h: the zero fields of lv ^ h...h
         const uint64_t e = lv ^ (kTileField1 * (uint64_t)h);
         uint64_t z = ~(((e & kTileFieldLo) + kTileFieldLo) | e) & kTileFieldHi;
-        // the events of one round touch disjoint positions (a sum that takes a
-        // partner is not taken itself), so up to four of them go at once: every
-        // load of a stage before the next stage, the stores last
         while (z) {
-            constexpr int EB = 4;
-            int fi[EB], sv[EB], jv[EB], kv[EB];
-            uint32_t ksv[EB], kjv[EB], kkv[EB];
-            int ssv[EB], skv[EB];
-            typename P::T a[EB], b[EB];
-#pragma unroll
-            for (int u = 0; u < EB; ++u) {
-                fi[u] = -1;
-                if (z) {
-                    fi[u] = (__ffsll((long long)z) - 1) / 5;
-                    z &= z - 1u;
-                }
-                sv[u] = tid + kTileThreads * (fi[u] < 0 ? 0 : fi[u]);
-                jv[u] = fi[u] >= 0 ? (int)nxt[sv[u]] : (int)kTileRet;
+            const int bit = __ffsll((long long)z) - 1;
+            z &= z - 1u;
+            const int i = bit / 5;
+            const int s = tid + kTileThreads * i;
+            const int j = nxt[s];
+            if (j & kTileRet) {   // retired by its left neighbour: it meets nothing any more
+                lv |= 31ull << (5 * i);
+                continue;
             }
-#pragma unroll
-            for (int u = 0; u < EB; ++u) {
-                kv[u] = n;
-                if (!(jv[u] & kTileRet)) {
-                    ksv[u] = K[sv[u]];
-                    kjv[u] = K[jv[u]];
-                    a[u] = x.vals[ksv[u] & kTilePMask];
-                    b[u] = x.vals[kjv[u] & kTilePMask];
-                    kv[u] = nxt[jv[u]];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < EB; ++u) {
-                kkv[u] = kKeyPad;
-                ssv[u] = 0;
-                skv[u] = 0;
-                if (!(jv[u] & kTileRet) && kv[u] < n) {
-                    kkv[u] = K[kv[u]];
-                    ssv[u] = st[sv[u]];
-                    skv[u] = st[kv[u]];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < EB; ++u) {
-                if (fi[u] < 0) continue;
-                const int sh5 = 5 * fi[u];
-                if (jv[u] & kTileRet) {   // retired by its left neighbour: it meets nothing any more
-                    lv |= 31ull << sh5;
-                    continue;
-                }
-                x.vals[ksv[u] & kTilePMask] = P::add(a[u], b[u]);
-                nxt[sv[u]] = (uint16_t)kv[u];
-                nxt[jv[u]] = (uint16_t)(kv[u] | kTileRet);
-                uint64_t m = 31u;
-                if (kv[u] < n && (kkv[u] >> kTilePBits) == (ksv[u] >> kTilePBits))
-                    m = (uint64_t)tile_bitlen((uint32_t)(ssv[u] ^ skv[u]));
-                lv = (lv & ~(31ull << sh5)) | (m << sh5);
-            }
+            const uint32_t kss = K[s], kjj = K[j];
+            const int ps = (int)(kss & kTilePMask), pj = (int)(kjj & kTilePMask);
+            x.vals[ps] = P::add(x.vals[ps], x.vals[pj]);
+            const int k = nxt[j];
+            nxt[s] = (uint16_t)k;
+            nxt[j] = (uint16_t)(k | kTileRet);
+            uint64_t m = 31u;
+            if (k < n && (K[k] >> kTilePBits) == (kss >> kTilePBits))
+                m = (uint64_t)tile_bitlen((uint32_t)(st[s] ^ st[k]));
+            lv = (lv & ~(31ull << (5 * i))) | (m << (5 * i));
         }
     }
     __syncthreads();
