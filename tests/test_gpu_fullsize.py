@@ -1,8 +1,9 @@
 """Parity at the full sizes of the workloads, with the default options (the
 launch configuration the benchmark times).
 
-* R-MAT scale 20, C = A*A, FP64 and FP32: nnz(C) is about 9.7e9, beyond
-  2^32, so the int64 output offsets of every numeric kernel are exercised.
+* R-MAT scale 20, C = A*A, FP64 and FP32 with the default options, and FP64
+  with every long row in column tiles: nnz(C) is about 9.7e9, beyond 2^32,
+  so the int64 output offsets of every numeric kernel are exercised.
   Every row length is compared with the oracle's symbolic pass; the values
   of sampled rows -- the 100 rows with the most products (up to ~9.7 M
   products and ~40 k lists), 400 seeded random rows, and the rows whose slice
@@ -49,31 +50,52 @@ def _release():
 @pytest.fixture(scope="module")
 def rmat20():
     A = I.rmat(20, 16)
-    return A, oracle.row_nprod(A, A)
+    return A, oracle.row_nprod(A, A), {}
 
 
-@pytest.mark.parametrize("prec,dtype", [("f64", np.float64), ("f32", np.float32)])
-def test_rmat_scale20_full_size(rmat20, prec, dtype):
-    A, nprod = rmat20
+def _rmat20_rows(A, nprod, rp):
+    top = np.argsort(-nprod, kind="stable")[:100]
+    rnd = I.rand_below(2020, 1, np.arange(400), A.rows)
+    marks = [2 ** 31 - 1, 2 ** 31, 2 ** 32 - 1, 2 ** 32, 2 ** 33]
+    return np.unique(np.concatenate([top, rnd, straddling_rows(rp, marks)]))
+
+
+def _rmat20_check(rmat20, prec, dtype, **opts):
+    A, nprod, cache = rmat20
     dA = brm.to_device(A, dtype=dtype)
-    C = brm.brm_spgemm_precise(dA, dA)
+    C = brm.brm_spgemm_precise(dA, dA, **opts)
     torch.cuda.synchronize()
     rp = C.rp.cpu().numpy()
     assert rp[-1] > 2 ** 32, "the workload no longer exercises 64-bit output offsets"
     if prec == "f64":
-        assert np.array_equal(np.diff(rp), oracle.symbolic_parallel(A, A, threads=THREADS))
-    top = np.argsort(-nprod, kind="stable")[:100]
-    rnd = I.rand_below(2020, 1, np.arange(400), A.rows)
-    marks = [2 ** 31 - 1, 2 ** 31, 2 ** 32 - 1, 2 ** 32, 2 ** 33]
-    rows = np.unique(np.concatenate([top, rnd, straddling_rows(rp, marks)]))
+        if "nnz" not in cache:
+            cache["nnz"] = oracle.symbolic_parallel(A, A, threads=THREADS)
+        assert np.array_equal(np.diff(rp), cache["nnz"])
+    rows = _rmat20_rows(A, nprod, rp)
     crp, col, val = device_rows(C, rows)
     del C, dA
     _release()
-    ref = oracle.alg1_parallel(A, A, rows, prec, THREADS)
-    assert_sample_exact(crp, col, val, ref)
+    key = (prec, rows.tobytes())
+    if key not in cache:
+        cache[key] = oracle.alg1_parallel(A, A, rows, prec, THREADS)
+    assert_sample_exact(crp, col, val, cache[key])
+    return rows, crp, val
+
+
+@pytest.mark.parametrize("prec,dtype", [("f64", np.float64), ("f32", np.float32)])
+def test_rmat_scale20_full_size(rmat20, prec, dtype):
+    A = rmat20[0]
+    rows, crp, val = _rmat20_check(rmat20, prec, dtype)
     if prec == "f64":
         g = oracle.gustavson_parallel(A, A, THREADS, rows, with_abs=True)
         assert rowwise_rel_err(crp, val, g.val, g.abs).max(initial=0.0) <= RTOL_F64
+
+
+def test_rmat_scale20_every_long_row_tiled(rmat20):
+    """The same checks with every long row of at most 65535 lists in column
+    tiles (long_window 2): the hub rows, up to ~40k lists, search their lists
+    block by block with their cursors in device memory."""
+    _rmat20_check(rmat20, "f64", np.float64, long_window=2)
 
 
 @pytest.fixture(scope="module")
