@@ -26,9 +26,9 @@
 //   columns) is the symbolic pass's result.  Consecutive tiles are grouped
 //   into spans of at least max(32768, 16 L) products.
 // Numeric (k_long_tile, persistent blocks taking spans from a counter):
-//   the block keeps one cursor per list of the row in shared memory (the
-//   next position of B_t* not yet consumed, its column, the list's end),
-//   found by binary search at the span's first column.  For a tile [c0, c1):
+//   the block keeps one cursor per list of the row (the next position of
+//   B_t* not yet consumed, its column, the list's end), found by binary
+//   search at the span's first column.  For a tile [c0, c1):
 //   1. every list's elements below c1 form its segment (a probe of the next
 //      four columns, for four lists at once, then a binary search bounded by
 //      c1 - column: B's columns are distinct), segments numbered in list
@@ -42,8 +42,9 @@
 //      every live sum takes the next live sum of its column when both have
 //      the same t >> h (left first), which is exactly what the rounds do to
 //      that column (a list without the column passes its partner through);
-//      every position is looked at by one thread, the rounds end when no
-//      sum can take a partner any more;
+//      every position is owned by one thread, which keeps the round in
+//      which its sum meets the next one, so a round touches only those
+//      sums; the rounds end when no sum can take a partner any more;
 //   5. the sums are written, compacted, at the tile's place in C.
 //   A hot tile (one cell of at most 128 columns with more than kTileP
 //   products) is taken in chunks of aligned list blocks [a 2^k, (a + 1) 2^k)
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
             j.win_n[r] = (int32_t)nwin;
             j.win_rownnz[r] = count;
             if (j.out_cnt != nullptr) j.out_cnt[row] = count;
-            // spans of consecutive windows: at least max(kWinSpanMin, 16 L)
+            // spans of consecutive tiles: at least max(kWinSpanMin, 16 L)
             // products each, on average
             const int64_t target = max(kWinSpanMin, (int64_t)kWinSpanPerList * ri.L);
             int64_t nws = prod > 0 ? target * nwin / prod : 1;
