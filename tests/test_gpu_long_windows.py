@@ -1,6 +1,9 @@
 """Long rows by column tiles (option long_window).
 
-A long row of at most 65535 lists is cut into column tiles of at most 2048
+By default (long_window 1) the long rows of at least 65536 products and at
+most 2048 lists take the tiles and the others the merge rounds; with
+long_window 2 (the tests' default here) every long row of at most 65535
+lists takes them.  A long row is cut into column tiles of at most 2048
 products planned from the symbolic pass's bitmap and per-cell product
 histogram; every tile's products are sorted by column in shared memory (a
 stable radix sort that keeps list order) and Algorithm 1's merge rounds run
@@ -89,6 +92,29 @@ def test_windows_are_taken():
     assert long_trace(R, R) == (1, 1)
     sym, num = long_trace(R, R, long_window=False)
     assert sym == 1 and num >= 1
+
+
+def test_default_split():
+    """The default options (long_window 1) send the long rows of at least
+    65536 products and at most 2048 lists to the tiles and the others to the
+    merge rounds, in the same passes, with the merge rounds' bits."""
+    R = I.rmat(16, 16, seed=86)
+    nprod = oracle.row_nprod(R, R)
+    L = np.diff(R.rp)
+    long = (nprod > 4096) | (L > 1024)
+    assert (long & (nprod >= 65536) & (L <= 2048)).any() and (long & (nprod < 65536)).any()
+    dR = brm.to_device(R)
+    brm.brm_trace_reset()
+    was = brm.brm_trace_enable(True)
+    C = brm.brm_spgemm_precise(dR, dR)
+    torch.cuda.synchronize()
+    t = brm.brm_trace_read()
+    brm.brm_trace_enable(was)
+    assert t["symbolic_tile"][1] == 1 and t["numeric_tile"][1] == 1
+    assert t["symbolic_long"][1] == 1 and t["numeric_long"][1] >= 1
+    same(C, run(R, R, long_window=False))
+    rows = np.sort(np.argsort(-nprod, kind="stable")[:20])
+    assert_rows_exact(C, oracle.alg1(R, R, rows), rows)
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
