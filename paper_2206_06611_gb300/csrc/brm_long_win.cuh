@@ -734,6 +734,10 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
     return nruns;
 }
 
+__device__ __forceinline__ void tile_prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // First position of B_t*[pos + 1 .. hi) whose column is c1 or more (hi if
 // none, also when the range is empty), by binary search.
 __device__ __forceinline__ int tile_seg_end(const int32_t *bcol, int pos, int hi, int c1) {
@@ -911,6 +915,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
                                 cpos[t] = e;
                                 ccol[t] = ncol;
                                 tpos[t - lb] = p;
+                                if (e < end) {
+                                    // where the list continues: the next tile's probes
+                                    // and products, fetched into L2 ahead of them
+                                    tile_prefetch_l2(ri.bcol + e);
+                                    tile_prefetch_l2(ri.bval + e);
+                                }
                             }
                             tlen[t - lb] = len;
                             ns += len > 0 ? 1 : 0;
