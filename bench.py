@@ -761,7 +761,7 @@ def run_profile(args):
         A = I.rmat(args.scale, 16) if args.workload == "rmat" else I.erdos_renyi(args.profile_n, 16)
         dA = brm.to_device(A, device="cuda:0")
         for _ in range(2):
-            lw = {"long_window": True} if args.long_window else {}   # else the library's default
+            lw = {} if args.long_window is None else {"long_window": args.long_window}   # else the library's default
             C = brm.brm_spgemm_precise(dA, dA, long_bucket=args.long_bucket, **lw)
             torch.cuda.synchronize()
             del C
@@ -793,9 +793,9 @@ def main():
                     help="--profile --workload batched: products of the mix (the first of the 512)")
     ap.add_argument("--long-bucket", action="store_true",
                     help="--profile: long rows' numeric pass by column buckets (option long_bucket)")
-    ap.add_argument("--long-window", action="store_true",
-                    help="--profile: every long row of at most 2048 lists by column tiles (option long_window 2; "
-                         "by default the library's split)")
+    ap.add_argument("--long-window", type=int, choices=[0, 1, 2], default=None,
+                    help="--profile: option long_window (0 merge rounds only, 1 the default split, 2 column tiles "
+                         "for every long row of at most 65535 lists)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
