@@ -586,6 +586,25 @@ def spgemm_sharded(A: DeviceCSR, B: DeviceCSR, group=None, **opts):
     return C, r0, r1, off, total
 
 
+def spgemm_sharded_backward(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, dC, r0: int, r1: int, group=None):
+    """The backward of spgemm_sharded on this rank: for its rows r0 .. r1-1
+    (C and dC: this rank's rows, local row pointer), dA of those rows' entries
+    of A (A's values A.rp[r0] .. A.rp[r1]-1, local to the rank) and dB of the
+    whole product -- every rank's dB of its rows (the library's backward on
+    the row slice, summed over those rows in increasing order) added up over
+    the group by one all-reduce, the exchange step of the row split.  The
+    ranks' partial sums are added in the collective's order, so dB may differ
+    from a single device's ordered sum in the last bits."""
+    import torch.distributed as dist
+    dA, dB = brm_spgemm_backward(row_slice(A, r0, r1), B, C, dC)
+    if dist.get_backend(group) == "nccl":
+        dist.all_reduce(dB, op=dist.ReduceOp.SUM, group=group)
+        return dA, dB
+    host = dB.cpu()
+    dist.all_reduce(host, op=dist.ReduceOp.SUM, group=group)
+    return dA, host.to(dB.device)
+
+
 # ---------------------------------------------------------------------------
 # tracing
 # ---------------------------------------------------------------------------
