@@ -295,7 +295,7 @@ struct Plan {
     int64_t long_split = 0;
 };
 
-// Whether the long rows of a product take the column tiles (brm_long_win.cuh):
+// Whether the long rows of a product take the column tiles (brm_long_tiles.cuh):
 // the option is on, the bucket option off, and B has at most 2^24 columns.
 bool tiles_apply(const brm_options &o, int64_t bcols) {
     return o.long_window && !o.long_bucket && bcols <= kLbMaxCols;
@@ -439,14 +439,14 @@ struct LongPlan {
     int32_t *ctr = nullptr;
 };
 
-// Long rows by column tiles (brm_long_win.cuh): the plan's arrays, kept from
+// Long rows by column tiles (brm_long_tiles.cuh): the plan's arrays, kept from
 // the pass that computes them (the symbolic pass of BRMerge-Precise and of
 // prepared batches; the numeric pass itself in BRMerge-Upper) to the numeric
 // pass.  They cover the long slots [long_split, count).
-struct WinPlan {
+struct TilePlan {
     bool on = false;
     bool planned = false;          // a pass has launched the plan kernel
-    WinRec *rec = nullptr;
+    TileRec *rec = nullptr;
     int64_t *base = nullptr;
     int32_t *n = nullptr, *nws = nullptr;
     int64_t *rownnz = nullptr;
@@ -458,19 +458,19 @@ struct WinPlan {
 };
 
 // The tiles' arrays, when the long rows of these passes take them.
-int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKind vnum, WinPlan &wp) {
-    wp = WinPlan{};
+int plan_tiles(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKind vnum, TilePlan &wp) {
+    wp = TilePlan{};
     const int64_t nl = (int64_t)pl.long_rows_h.size(), s0 = pl.long_split;
     if (nl == s0 || !tiles_apply(o, bcols)) return BRM_OK;
     const int64_t nt = nl - s0;
     std::vector<int64_t> base((size_t)nt + 1, 0);
     int64_t spans = 0, maxL = 0;
     for (int64_t s = 0; s < nt; ++s) {
-        base[s + 1] = base[s] + win_cap(pl.long_nprod_h[s0 + s], bcols);
-        spans += win_span_cap(pl.long_nprod_h[s0 + s]);
+        base[s + 1] = base[s] + tile_cap(pl.long_nprod_h[s0 + s], bcols);
+        spans += tile_span_cap(pl.long_nprod_h[s0 + s]);
         maxL = std::max<int64_t>(maxL, pl.long_L_h[s0 + s]);
     }
-    wp.grid = long_win_grid(vnum == kIdx ? kF64 : vnum);
+    wp.grid = long_tile_grid(vnum == kIdx ? kF64 : vnum);
     int rc;
     if ((rc = get(mem, wp.base, (size_t)nt + 1, "tile offsets"))) return rc;
     if ((rc = get(mem, wp.rec, (size_t)std::max<int64_t>(base[nt], 1), "tiles"))) return rc;
@@ -490,22 +490,22 @@ int plan_win(Mem &mem, const Plan &pl, const brm_options &o, int64_t bcols, VKin
 }
 
 // The tile fields of a long-row job.
-void win_job(RowJob &jb, const WinPlan &wp, bool plan_here) {
-    jb.win = wp.rec;
-    jb.win_base = wp.base;
-    jb.win_n = wp.n;
-    jb.win_nws = wp.nws;
-    jb.win_rownnz = wp.rownnz;
-    jb.win_spans = wp.spans;
-    jb.win_ctr = wp.ctr;
-    jb.win_cur = wp.cur;
-    jb.win_maxL = wp.maxL;
-    jb.win_grid = wp.grid;
-    jb.win_plan = plan_here ? 1 : 0;
+void tile_job(RowJob &jb, const TilePlan &wp, bool plan_here) {
+    jb.tiles = wp.rec;
+    jb.tile_base = wp.base;
+    jb.tile_n = wp.n;
+    jb.tile_nws = wp.nws;
+    jb.tile_rownnz = wp.rownnz;
+    jb.tile_spans = wp.spans;
+    jb.tile_ctr = wp.ctr;
+    jb.tile_cur = wp.cur;
+    jb.tile_maxL = wp.maxL;
+    jb.tile_grid = wp.grid;
+    jb.tile_plan = plan_here ? 1 : 0;
 }
 
 int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t bcols, LongPlan &lp,
-              bool persistent = true, const WinPlan *wp = nullptr) {
+              bool persistent = true, const TilePlan *wp = nullptr) {
     // with column tiles, only the slots before long_split merge in rounds
     const int64_t nl = (wp && wp->on) ? pl.long_split : (int64_t)pl.long_rows_h.size();
     lp.starts.clear();
@@ -608,7 +608,7 @@ int plan_long(Mem &mem, VKind v, const Plan &pl, const brm_options &o, int64_t b
 // Kernel launches of one pass over every bin (no host synchronisation, no
 // allocation: a numeric pass of a prepared plan can be captured in a graph).
 int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cudaStream_t st, bool trace,
-                const WinPlan *wp = nullptr) {
+                const TilePlan *wp = nullptr) {
     for (int b = kBinReg0; b <= kBinBlock; ++b) {
         RowJob jb = j;
         jb.rows = pl.rows + pl.base[b];
@@ -624,7 +624,7 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
         jb.rows = pl.long_rows_s + pl.long_split;
         jb.count = (int32_t)((int64_t)pl.long_rows_h.size() - pl.long_split);
         jb.slot_nprod = pl.long_nprod_s + pl.long_split;
-        win_job(jb, *wp, v == kIdx || !wp->planned);
+        tile_job(jb, *wp, v == kIdx || !wp->planned);
         PhaseScope ps(trace ? (v == kIdx ? kPhSymTile : kPhNumTile) : -1, st);
         BRM_CUDA(launch_rows(v, kBinLong, jb, st));
     }
@@ -658,7 +658,7 @@ int launch_pass(VKind v, const Plan &pl, const LongPlan &lp, const RowJob &j, cu
 
 // One BRMerge pass (symbolic or numeric) over all bins.
 int run_pass(Mem &mem, VKind v, const Plan &pl, const brm_options &o, RowJob j, bool persistent = true,
-             WinPlan *wp = nullptr) {
+             TilePlan *wp = nullptr) {
     LongPlan lp;
     int rc = plan_long(mem, v, pl, o, j.bcols, lp, persistent, wp);
     if (rc) return rc;
@@ -717,13 +717,13 @@ struct PermBuf {
 };
 
 int symbolic_into(Mem &mem, const Src &src, const brm_options &o, Plan &pl, int64_t *row_ptr, int64_t *nnz,
-                  PermBuf *pb = nullptr, WinPlan *wp = nullptr) {
+                  PermBuf *pb = nullptr, TilePlan *wp = nullptr) {
     const int64_t m = src.m;
     int64_t *row_nnz;
     int rc = get(mem, row_nnz, (size_t)std::max<int64_t>(m, 1), "row counts");
     if (rc) return rc;
     if ((rc = make_plan(mem, src, o, pl, nullptr, row_nnz))) return rc;
-    if (wp && (rc = plan_win(mem, pl, o, src.bcols, value_kind(src.dtype, o), *wp))) return rc;
+    if (wp && (rc = plan_tiles(mem, pl, o, src.bcols, value_kind(src.dtype, o), *wp))) return rc;
     void *tmp;
     if (!(tmp = mem.get(scan_tmp_bytes(m)))) return fail(BRM_ERR_OOM, "scan workspace");
     RowJob j = base_job(src, o);
@@ -774,7 +774,7 @@ int precise(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_option
     int64_t nnz = 0;
     const Src src = src_of(A, B);
     PermBuf pb;
-    WinPlan wp;
+    TilePlan wp;
     if ((rc = symbolic_into(mem, src, o, pl, rp, &nnz, &pb, &wp))) return rc;
     int32_t *col;
     if ((rc = get_own(mem, col, (size_t)std::max<int64_t>(nnz, 1), "C.col_idx"))) return rc;
@@ -981,8 +981,8 @@ int upper(const brm_csr *A, const brm_csr *B, brm_csr_out *C, const brm_options 
     if ((rc = get(mem, err, 1, "error flag"))) return rc;
     BRM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), mem.st));
     j.err = err;
-    WinPlan wp;
-    if ((rc = plan_win(mem, pl, o, src.bcols, value_kind(A->dtype, o), wp))) return rc;
+    TilePlan wp;
+    if ((rc = plan_tiles(mem, pl, o, src.bcols, value_kind(A->dtype, o), wp))) return rc;
     if ((rc = run_pass(mem, value_kind(A->dtype, o), pl, o, j, true, &wp))) return rc;
     // step 5: prefix sum of the row sizes, allocation of C
     if ((rc = get_own(mem, rp, (size_t)m + 1, "C.row_ptr"))) return rc;
@@ -1087,7 +1087,7 @@ struct brm_batch {
     brm::LongPlan lp;
     brm::RowJob job{};
     brm::PermBuf pb;
-    brm::WinPlan wp;
+    brm::TilePlan wp;
     brm::VKind v = brm::kF64;
     int32_t count = 0;
     int64_t nnz = 0;

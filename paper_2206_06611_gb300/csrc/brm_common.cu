@@ -387,9 +387,9 @@ extern size_t long_bytes_f64(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_f32(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_f32c(int64_t n, int64_t L, bool bucket);
 extern size_t long_bytes_idx(int64_t n, int64_t L, bool bucket);
-extern int win_grid_f64();
-extern int win_grid_f32();
-extern int win_grid_f32c();
+extern int tile_grid_f64();
+extern int tile_grid_f32();
+extern int tile_grid_f32c();
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st) {
     switch (v) {
@@ -409,11 +409,11 @@ size_t long_row_bytes_for(VKind v, int64_t n, int64_t L, bool bucket) {
     }
 }
 
-int long_win_grid(VKind v) {
+int long_tile_grid(VKind v) {
     switch (v) {
-        case kF64: return win_grid_f64();
-        case kF32: return win_grid_f32();
-        case kF32C: return win_grid_f32c();
+        case kF64: return tile_grid_f64();
+        case kF32: return tile_grid_f32();
+        case kF32C: return tile_grid_f32c();
         default: return 0;
     }
 }

@@ -218,22 +218,22 @@ struct RowJob {
     // from the counter (zero at launch), in the arena at arena_off[b]
     int32_t *long_ctr;
     int32_t long_grid;
-    // long rows by column tiles (brm_long_win.cuh): per long slot, where its
+    // long rows by column tiles (brm_long_tiles.cuh): per long slot, where its
     // tiles start (count + 1 entries), how many it has, tiles per span, the
     // row's distinct columns; the span list and its two counters (spans
     // written, spans taken); per block of the numeric kernel, cursors for the
-    // rows of more than kTileSmemL lists (3 x win_maxL ints, or null)
-    struct WinRec *win;
-    const int64_t *win_base;
-    int32_t *win_n;
-    int32_t *win_nws;
-    int64_t *win_rownnz;
-    int2 *win_spans;
-    unsigned long long *win_ctr;
-    int32_t *win_cur;
-    int32_t win_maxL;
-    int32_t win_grid;       // persistent blocks of the numeric kernel
-    int32_t win_plan;       // 1: this pass computes the plan first (symbolic pass, or Upper)
+    // rows of more than kTileSmemL lists (3 x tile_maxL ints, or null)
+    struct TileRec *tiles;
+    const int64_t *tile_base;
+    int32_t *tile_n;
+    int32_t *tile_nws;
+    int64_t *tile_rownnz;
+    int2 *tile_spans;
+    unsigned long long *tile_ctr;
+    int32_t *tile_cur;
+    int32_t tile_maxL;
+    int32_t tile_grid;       // persistent blocks of the numeric kernel
+    int32_t tile_plan;       // 1: this pass computes the plan first (symbolic pass, or Upper)
 };
 
 // The inputs one output row needs: its row of A (columns and values from the

@@ -63,14 +63,14 @@ constexpr int kLbSlots = 65536;
 constexpr int kLbHotPerSm = 2;
 __host__ __device__ constexpr int64_t lb_work_cap(int64_t n) { return n / (kLbUnit + 1) + 1; }
 
-// Long rows by column tiles (brm_long_win.cuh): a tile holds at most kTileP
+// Long rows by column tiles (brm_long_tiles.cuh): a tile holds at most kTileP
 // products (one thread block of kTileThreads sorts them) unless it is a single
-// cell of at most kWinCellMax columns (a "hot" tile, taken in chunks); the
-// plan cuts pieces every kWinH products and packs them into tiles; at most
-// kWinCells cells per bitmap window of kWinBitmapCols columns; rows of at most
+// cell of at most kTileCellMax columns (a "hot" tile, taken in chunks); the
+// plan cuts pieces every kTilePiece products and packs them into tiles; at most
+// kTileCells cells per bitmap window of kTileBitmapCols columns; rows of at most
 // kTileMaxL lists and at least kTileMinNprod products (others keep the merge
 // rounds); spans of at least
-// max(kWinSpanMin, kWinSpanPerList * L) products.
+// max(kTileSpanMin, kTileSpanPerList * L) products.
 constexpr int kTileP = 2048;
 constexpr int kTilePBits = 11;
 constexpr int kTileThreads = 256;
@@ -78,38 +78,38 @@ constexpr int kTileMaxL = 65535;     // 16-bit list index
 constexpr int kTileSmemL = 2048;     // lists whose cursors fit shared memory (more: device memory)
 // long rows of fewer products keep the merge rounds (measured faster there)
 constexpr int64_t kTileMinNprod = 65536;
-constexpr int kWinH = 256;
-constexpr int64_t kWinBitmapCols = (int64_t)1 << 20;
-constexpr int kWinCells = 8192;
-constexpr int kWinCellMax = (int)(kWinBitmapCols / kWinCells);
-constexpr int64_t kWinSpanMin = 32768;
-constexpr int kWinSpanPerList = 16;
+constexpr int kTilePiece = 256;
+constexpr int64_t kTileBitmapCols = (int64_t)1 << 20;
+constexpr int kTileCells = 8192;
+constexpr int kTileCellMax = (int)(kTileBitmapCols / kTileCells);
+constexpr int64_t kTileSpanMin = 32768;
+constexpr int kTileSpanPerList = 16;
 static_assert((1 << kTilePBits) == kTileP, "a tile position fits the key's low bits");
 static_assert(kTileSmemL <= kTileP, "a tile that fits one sort has at most kTileP segments");
-static_assert(kWinCellMax == 128, "cells are at most 128 columns wide");
-static_assert((((kWinBitmapCols - 1) << kTilePBits) | (kTileP - 1)) <= 0xffffffffLL, "key = column offset and position");
+static_assert(kTileCellMax == 128, "cells are at most 128 columns wide");
+static_assert((((kTileBitmapCols - 1) << kTilePBits) | (kTileP - 1)) <= 0xffffffffLL, "key = column offset and position");
 
-// One window of a long row: first column, products, and the number of the
+// One tile of a long row: first column, products, and the number of the
 // row's distinct columns before it (its output offset inside the row).
-struct WinRec {
+struct TileRec {
     int32_t c0;
     int32_t np;
     int64_t off;
 };
-static_assert(sizeof(WinRec) == 16, "window record size");
+static_assert(sizeof(TileRec) == 16, "tile record size");
 
-// Windows a row of n products can produce over B's columns (ncols): every
-// bitmap window holds at most 3 n_w / kWinH + 1 cuts, and never more than its
-// cells.
-__host__ __device__ constexpr int64_t win_cap(int64_t n, int64_t ncols) {
-    const int64_t nbw = ncols > 0 ? (ncols + kWinBitmapCols - 1) / kWinBitmapCols : 1;
-    const int64_t a = 3 * ((n + kWinH - 1) / kWinH) + nbw;
-    const int64_t b = nbw * kWinCells;
+// Tiles a row of n products can produce over B's columns (ncols): every
+// bitmap window holds at most 3 n_w / kTilePiece + 1 pieces (and tiles), and
+// never more than its cells.
+__host__ __device__ constexpr int64_t tile_cap(int64_t n, int64_t ncols) {
+    const int64_t nbw = ncols > 0 ? (ncols + kTileBitmapCols - 1) / kTileBitmapCols : 1;
+    const int64_t a = 3 * ((n + kTilePiece - 1) / kTilePiece) + nbw;
+    const int64_t b = nbw * kTileCells;
     return a < b ? a : b;
 }
 
-// Spans a row of n products can produce: at most 2 n / kWinSpanMin + 2.
-__host__ __device__ constexpr int64_t win_span_cap(int64_t n) { return 2 * (n / kWinSpanMin) + 2; }
+// Spans a row of n products can produce: at most 2 n / kTileSpanMin + 2.
+__host__ __device__ constexpr int64_t tile_span_cap(int64_t n) { return 2 * (n / kTileSpanMin) + 2; }
 
 // Kernel phases recorded by the tracer (brm_trace_*).
 enum Phase {
@@ -125,8 +125,8 @@ enum VKind { kIdx = 0, kF64 = 1, kF32 = 2, kF32C = 3 };
 
 cudaError_t launch_rows(VKind v, int bin, const RowJob &j, cudaStream_t st);
 size_t long_row_bytes_for(VKind v, int64_t nprod, int64_t L, bool bucket);
-// blocks of the long-row window kernel of a value kind (0 for kIdx)
-int long_win_grid(VKind v);
+// blocks of the long-row tile kernel of a value kind (0 for kIdx)
+int long_tile_grid(VKind v);
 
 // Statistics written by the binning kernels.
 struct BinStats {

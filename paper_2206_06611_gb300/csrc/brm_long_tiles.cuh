@@ -11,14 +11,14 @@
 // block in shared memory, instead of one block merging the whole row round by
 // round through device memory.
 //
-// Plan (k_win_plan, one block per long row, index-only work):
+// Plan (k_tile_plan, one block per long row, index-only work):
 //   the row's columns are set in a shared-memory bitmap (one window of 2^20
 //   columns of B at a time) and its products counted per cell of 2^sh
 //   columns (at most 8192 cells per bitmap window, so a cell is at most 128
 //   columns wide).  Consecutive cells are grouped into pieces -- a cut
-//   wherever the running product count crosses a multiple of kWinH, and
-//   before and after every cell of more than kWinH products, so that a piece
-//   holds fewer than 2 kWinH products unless it is a single cell -- and the
+//   wherever the running product count crosses a multiple of kTilePiece, and
+//   before and after every cell of more than kTilePiece products, so that a piece
+//   holds fewer than 2 kTilePiece products unless it is a single cell -- and the
 //   pieces are packed greedily into tiles of at most kTileP products (a
 //   piece of more is a single cell, and a tile of its own).  Every tile
 //   records its first column, its products and where its output starts
@@ -72,12 +72,12 @@
 
 namespace brm {
 
-static_assert(kLsWinBits == kWinBitmapCols, "the plan's bitmap window is the symbolic kernel's");
-static_assert(kWinCells % kLsThreads == 0, "plan: whole cells per thread");
+static_assert(kLsWinBits == kTileBitmapCols, "the plan's bitmap window is the symbolic kernel's");
+static_assert(kTileCells % kLsThreads == 0, "plan: whole cells per thread");
 
 // Cell shift for a bitmap window of wn columns: the smallest sh with
-// ceil(wn / 2^sh) <= kWinCells.
-__host__ __device__ constexpr int win_shift(int64_t wn) {
+// ceil(wn / 2^sh) <= kTileCells.
+__host__ __device__ constexpr int tile_cell_shift(int64_t wn) {
     const int b = lb_bitlen((uint64_t)(wn > 1 ? wn - 1 : 0));
     return b > 13 ? b - 13 : 0;
 }
@@ -88,7 +88,7 @@ constexpr int kTileLevels = 16;
 static_assert((1 << kTileLevels) == kTileMaxL + 1, "list levels");
 constexpr int kTileChunkLevels = 11;
 static_assert((1 << kTileChunkLevels) == kTileSmemL, "a list block is an aligned subtree");
-constexpr uint32_t kWinEmpty = 0xffffffffu;   // carried state of a column that has no sum yet
+constexpr uint32_t kTileEmpty = 0xffffffffu;   // carried state of a column that has no sum yet
 constexpr uint32_t kTilePMask = (1u << kTilePBits) - 1u;
 constexpr uint16_t kTileRet = 0x8000u;         // a retired position of the merge rounds
 static_assert(kTileP < kTileRet, "positions fit 15 bits");
@@ -108,7 +108,7 @@ static_assert(kTileWords % 32 == 0, "whole words per lane");
 // Plan
 // ---------------------------------------------------------------------------
 template <class P>
-__global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
+__global__ void __launch_bounds__(kLsThreads, 1) k_tile_plan(RowJob j) {
     extern __shared__ __align__(16) uint32_t bm[];
     uint32_t *hist = bm + kLsWinBits / 32;
     __shared__ int32_t s_q0[kLsThreads];
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
     __shared__ int ws[kLsThreads / 32 + 1];
     __shared__ int64_t s_span[2];
     __shared__ int64_t s_nwin;
-    constexpr int NT = kLsThreads, PER = kWinCells / NT, K = 8;
+    constexpr int NT = kLsThreads, PER = kTileCells / NT, K = 8;
     BlockGrp<NT> g;
     g.ws = ws;
     const int tid = (int)threadIdx.x;
@@ -124,13 +124,13 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
     for (int r = blockIdx.x; r < j.count; r += gridDim.x) {
         const int row = j.rows[r];
         const RowIn<float> ri = row_in<float>(j, row);
-        WinRec *wr = j.win + j.win_base[r];
-        const int64_t cap = j.win_base[r + 1] - j.win_base[r];
+        TileRec *wr = j.tiles + j.tile_base[r];
+        const int64_t cap = j.tile_base[r + 1] - j.tile_base[r];
         int64_t count = 0, prod = 0, nwin = 0;
         for (int64_t w0 = 0; w0 < ncols; w0 += kLsWinBits) {
             const uint32_t wn = (uint32_t)(ncols - w0 < kLsWinBits ? ncols - w0 : kLsWinBits);
             const int words = (int)((wn + 31) >> 5);
-            const int sh = win_shift(wn);
+            const int sh = tile_cell_shift(wn);
             const int nc = (int)(((int64_t)wn + (1 << sh) - 1) >> sh);
             for (int i = tid; i < words; i += NT) bm[i] = 0u;
             for (int i = tid; i < nc; i += NT) hist[i] = 0u;
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                 g.sync();
                 continue;
             }
-            // cuts: the first cell, around cells of more than kWinH products,
-            // and where the running count crosses a multiple of kWinH
+            // cuts: the first cell, around cells of more than kTilePiece products,
+            // and where the running count crosses a multiple of kTilePiece
             unsigned flags = 0;
             int nflag = 0;
             {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                     const int d = cb + e;
                     if (d < nc) {
                         const int Sp = S - pc;
-                        const bool cut = d == 0 || cp[e] > kWinH || pc > kWinH || (S / kWinH) != (Sp / kWinH);
+                        const bool cut = d == 0 || cp[e] > kTilePiece || pc > kTilePiece || (S / kTilePiece) != (Sp / kTilePiece);
                         if (cut) {
                             flags |= 1u << e;
                             ++nflag;
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
             // the bitmap's memory now holds the cut list and the cells'
             // exclusive product and distinct-column counts
             int32_t *ul = reinterpret_cast<int32_t *>(bm);
-            int32_t *Sc = ul + kWinCells + 1;
-            int32_t *Dc = Sc + kWinCells + 1;
+            int32_t *Sc = ul + kTileCells + 1;
+            int32_t *Dc = Sc + kTileCells + 1;
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
                 const int d = cb + e;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
                     int q1 = q + 1;
                     while (q1 < ftot && Sc[ul[q1 + 1]] - Sc[d0] <= kTileP) ++q1;
                     if (nw < cap) {
-                        WinRec rec;
+                        TileRec rec;
                         rec.c0 = (int32_t)(w0 + ((int64_t)d0 << sh));
                         rec.np = Sc[ul[q1]] - Sc[d0];
                         rec.off = count + Dc[d0];
@@ -265,28 +265,28 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
             g.sync();   // the cut list is read before the bitmap is cleared again
         }
         if (tid == 0) {
-            j.win_n[r] = (int32_t)nwin;
-            j.win_rownnz[r] = count;
+            j.tile_n[r] = (int32_t)nwin;
+            j.tile_rownnz[r] = count;
             if (j.out_cnt != nullptr) j.out_cnt[row] = count;
-            // spans of consecutive tiles: at least max(kWinSpanMin, 16 L)
+            // spans of consecutive tiles: at least max(kTileSpanMin, 16 L)
             // products each, on average
-            const int64_t target = max(kWinSpanMin, (int64_t)kWinSpanPerList * ri.L);
+            const int64_t target = max(kTileSpanMin, (int64_t)kTileSpanPerList * ri.L);
             int64_t nws = prod > 0 ? target * nwin / prod : 1;
             if (nws > nwin) nws = nwin;
             if (nws < 1) nws = 1;
-            j.win_nws[r] = (int32_t)nws;
+            j.tile_nws[r] = (int32_t)nws;
             int64_t nsp = (nwin + nws - 1) / nws;
-            const int64_t scap = win_span_cap(j.slot_nprod[r]);
+            const int64_t scap = tile_span_cap(j.slot_nprod[r]);
             if (nsp > scap) {
-                if (j.err != nullptr) atomicOr(j.err, 2u);   // cannot happen: see win_span_cap
+                if (j.err != nullptr) atomicOr(j.err, 2u);   // cannot happen: see tile_span_cap
                 nsp = scap;
             }
-            s_span[0] = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(j.win_ctr),
+            s_span[0] = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(j.tile_ctr),
                                            (unsigned long long)nsp);
             s_span[1] = nsp;
         }
         g.sync();
-        for (int64_t k = tid; k < s_span[1]; k += NT) j.win_spans[s_span[0] + k] = make_int2(r, (int)k);
+        for (int64_t k = tid; k < s_span[1]; k += NT) j.tile_spans[s_span[0] + k] = make_int2(r, (int)k);
         g.sync();
     }
 }
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) k_win_plan(RowJob j) {
 // the column in their order.  Pending sums live in memory with a stride
 // (the carried stacks of a hot tile's columns).
 template <class P, class Ptr>
-struct WinStack {
+struct LevelStack {
     using T = typename P::T;
     Ptr pend;          // pend[(h - 1) * stride]
     int stride;
@@ -363,11 +363,11 @@ struct TileSmem {
     static constexpr size_t kVals = kKeyB + 4 * kTileP;                             // T[kTileP]
     static constexpr size_t kLidx = kVals + sizeof(T) * kTileP;                     // uint16[kTileP]
     static constexpr size_t kCnt = align_up(kLidx + 2 * kTileP, 16);                // uint32[kTileNW][256]
-    static constexpr size_t kHTop = align_up(kCnt + 4 * kTileNW * 256, 16);         // T[kWinCellMax]
-    static constexpr size_t kHPend = kHTop + sizeof(T) * kWinCellMax;               // T[kTileLevels][kWinCellMax]
-    static constexpr size_t kHMask = kHPend + sizeof(T) * kTileLevels * kWinCellMax;   // uint32[kWinCellMax]
-    static constexpr size_t kHLast = kHMask + 4 * kWinCellMax;                      // int32[kWinCellMax]
-    static constexpr size_t kBytes = align_up(kHLast + 4 * kWinCellMax, 16);
+    static constexpr size_t kHTop = align_up(kCnt + 4 * kTileNW * 256, 16);         // T[kTileCellMax]
+    static constexpr size_t kHPend = kHTop + sizeof(T) * kTileCellMax;               // T[kTileLevels][kTileCellMax]
+    static constexpr size_t kHMask = kHPend + sizeof(T) * kTileLevels * kTileCellMax;   // uint32[kTileCellMax]
+    static constexpr size_t kHLast = kHMask + 4 * kTileCellMax;                      // int32[kTileCellMax]
+    static constexpr size_t kBytes = align_up(kHLast + 4 * kTileCellMax, 16);
     static_assert(kTileP >= kTileSmemL, "the search scratch of a list block fits a key buffer");
 };
 
@@ -546,16 +546,16 @@ __device__ __forceinline__ void tile_emit(const TileCtx<P> &x, bool hot, int tb,
         }
         return;
     }
-    if (col >= (uint32_t)kWinCellMax) {
+    if (col >= (uint32_t)kTileCellMax) {
         atomicOr(x.err, 2u);   // cannot happen: a hot tile is one cell
         return;
     }
     const uint32_t hm = x.hmask[col];
-    if (hm == kWinEmpty) {
+    if (hm == kTileEmpty) {
         x.htop[col] = v;
         x.hmask[col] = 0u;
     } else {
-        WinStack<P, T *> st{x.hpend + col, kWinCellMax, x.htop[col], hm, 0};
+        LevelStack<P, T *> st{x.hpend + col, kTileCellMax, x.htop[col], hm, 0};
         st.push(v, tile_bitlen((uint32_t)(x.hlast[col] ^ tb)));
         x.htop[col] = st.top;
         x.hmask[col] = st.mask;
@@ -618,9 +618,9 @@ __device__ int tile_chunk(const TileCtx<P> &x, int sa, int sb, int pos0, int n, 
             const int p = tid + kTileThreads * i;
             if (q[i] >= 0) {
                 uint32_t co = (uint32_t)(c[i] - x.c0);
-                if (co >= (uint32_t)kWinBitmapCols) {
+                if (co >= (uint32_t)kTileBitmapCols) {
                     atomicOr(x.err, 2u);   // cannot happen: a tile lies inside one bitmap window
-                    co = (uint32_t)kWinBitmapCols - 1u;
+                    co = (uint32_t)kTileBitmapCols - 1u;
                 }
                 x.keyA[p] = (co << kTilePBits) | (uint32_t)p;
                 x.vals[p] = P::mul(a[i], v[i]);
@@ -774,8 +774,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
     BlockGrp<NT> g;
     g.ws = ws;
     const uint64_t keep = l2_keep_policy();
-    const unsigned long long nspans = *reinterpret_cast<const unsigned long long *>(j.win_ctr);
-    unsigned long long *taken = reinterpret_cast<unsigned long long *>(j.win_ctr) + 1;
+    const unsigned long long nspans = *reinterpret_cast<const unsigned long long *>(j.tile_ctr);
+    unsigned long long *taken = reinterpret_cast<unsigned long long *>(j.tile_ctr) + 1;
 
     TileCtx<P> x;
     x.segq = segq;
@@ -803,19 +803,19 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
         const unsigned long long s = s_span;
         __syncthreads();
         if (s >= nspans) break;
-        const int2 sp = j.win_spans[s];
+        const int2 sp = j.tile_spans[s];
         const int r = sp.x, row = j.rows[r];
         const RowIn<In> ri = row_in<In>(j, row);
         const int L = ri.L;
-        const int nwin = j.win_n[r], nws = j.win_nws[r];
+        const int nwin = j.tile_n[r], nws = j.tile_nws[r];
         const int w0 = sp.y * nws, w1 = min(nwin, w0 + nws);
-        const WinRec *wr = j.win + j.win_base[r];
-        const int64_t rownnz = j.win_rownnz[r];
+        const TileRec *wr = j.tiles + j.tile_base[r];
+        const int64_t rownnz = j.tile_rownnz[r];
         const int64_t obase = j.out_rp[row];
         const int64_t slot = j.out_rp[row + 1] - obase;
         if (sp.y == 0 && tid == 0 && (rownnz > slot || (j.exact && rownnz != slot))) atomicOr(j.err, 1u);
         if (w0 >= w1) continue;
-        if (L > kTileMaxL || (L > kTileSmemL && (j.win_cur == nullptr || L > j.win_maxL))) {
+        if (L > kTileMaxL || (L > kTileSmemL && (j.tile_cur == nullptr || L > j.tile_maxL))) {
             if (tid == 0) atomicOr(j.err, 2u);   // cannot happen: the host gives such rows the merge rounds
             continue;
         }
@@ -826,10 +826,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
         // slice of device memory
         int32_t *cpos = cpos_s, *ccol = ccol_s, *cend = cend_s;
         if (L > kTileSmemL) {
-            int32_t *cg = j.win_cur + (size_t)blockIdx.x * 3 * (size_t)j.win_maxL;
+            int32_t *cg = j.tile_cur + (size_t)blockIdx.x * 3 * (size_t)j.tile_maxL;
             cpos = cg;
-            ccol = cg + j.win_maxL;
-            cend = cg + 2 * (size_t)j.win_maxL;
+            ccol = cg + j.tile_maxL;
+            cend = cg + 2 * (size_t)j.tile_maxL;
         }
 
         // cursors at the span's first column
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
         __syncthreads();
 
         for (int w = w0; w < w1; ++w) {
-            const WinRec rec = wr[w];
+            const TileRec rec = wr[w];
             if (rec.np == 0) continue;
             const int c0 = rec.c0;
             const int c1 = w + 1 < nwin ? wr[w + 1].c0 : INT_MAX;
@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
             if (rec.off + x.expect > slot) x.expect = rec.off < slot ? slot - rec.off : 0;   // flagged above
             const bool hot = rec.np > kTileP;
             if (hot)
-                for (int c = tid; c < kWinCellMax; c += NT) x.hmask[c] = kWinEmpty;
+                for (int c = tid; c < kTileCellMax; c += NT) x.hmask[c] = kTileEmpty;
             // the lists in blocks of kTileSmemL: a tile that fits one sort
             // gathers every block's segments into one table (at most kTileP of
             // them: a segment holds a product), a hot tile takes each block's
@@ -1006,11 +1006,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
             __syncthreads();
             bool has = false;
             T v = T();
-            if (tid < kWinCellMax) {
+            if (tid < kTileCellMax) {
                 const uint32_t hm = x.hmask[tid];
-                has = hm != kWinEmpty;
+                has = hm != kTileEmpty;
                 if (has) {
-                    const WinStack<P, T *> st{x.hpend + tid, kWinCellMax, x.htop[tid], hm, 0};
+                    const LevelStack<P, T *> st{x.hpend + tid, kTileCellMax, x.htop[tid], hm, 0};
                     v = st.finish();
                 }
             }
@@ -1032,7 +1032,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_long_tile(RowJob j) {
 // ---------------------------------------------------------------------------
 // Blocks of the numeric kernel: every SM's resident blocks.
 template <class P>
-int win_grid_t() {
+int tile_grid_t() {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1049,14 +1049,14 @@ int win_grid_t() {
 // it: the symbolic pass, or BRMerge-Upper's numeric pass), then -- for a
 // value pass -- the tiles.
 template <class P>
-cudaError_t launch_long_win(const RowJob &j, cudaStream_t st) {
+cudaError_t launch_long_tiles(const RowJob &j, cudaStream_t st) {
     cudaError_t e;
-    if (j.win_plan) {
-        const size_t smb = (size_t)kLsWinBits / 8 + sizeof(uint32_t) * kWinCells;
-        auto kp = k_win_plan<PIdx>;
+    if (j.tile_plan) {
+        const size_t smb = (size_t)kLsWinBits / 8 + sizeof(uint32_t) * kTileCells;
+        auto kp = k_tile_plan<PIdx>;
         if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb)) != cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(j.win_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(j.tile_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
         kp<<<j.count, kLsThreads, smb, st>>>(j);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1066,8 +1066,8 @@ cudaError_t launch_long_win(const RowJob &j, cudaStream_t st) {
         auto kw = k_long_tile<P>;
         if ((e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(j.win_ctr + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-        kw<<<j.win_grid, kTileThreads, sm, st>>>(j);
+        if ((e = cudaMemsetAsync(j.tile_ctr + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        kw<<<j.tile_grid, kTileThreads, sm, st>>>(j);
         g_launches.fetch_add(1, std::memory_order_relaxed);
     }
     return cudaGetLastError();

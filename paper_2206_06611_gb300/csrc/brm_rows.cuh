@@ -15,7 +15,7 @@
 #include "brm_engine.cuh"
 #include "brm_internal.h"
 #include "brm_long_rows.cuh"
-#include "brm_long_win.cuh"
+#include "brm_long_tiles.cuh"
 #include "brm_reg_rows.cuh"
 
 namespace brm {
@@ -299,8 +299,8 @@ cudaError_t launch_rows_t(int bin, const RowJob &j, cudaStream_t st) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
         return cudaGetLastError();
     }
-    // long rows: by column windows, by column buckets, or one block per row
-    if (j.win != nullptr) return launch_long_win<P>(j, st);
+    // long rows: by column tiles, by column buckets, or one block per row
+    if (j.tiles != nullptr) return launch_long_tiles<P>(j, st);
     if (j.long_bucket) return launch_long_bucket<P>(j, st);
     {
         const size_t sm = TiledRoundSmem<P, kLongThreads, long_k<P>()>::kBytes;

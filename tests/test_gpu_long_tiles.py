@@ -67,7 +67,7 @@ def long_trace(A, B, **kw):
 
 
 @pytest.mark.parametrize("mode,dtype,comp", MODES)
-def test_windows_match_rounds_and_oracle(mode, dtype, comp):
+def test_tiles_match_rounds_and_oracle(mode, dtype, comp):
     A, B = bins_matrix(seed=7)
     ref = oracle.alg1(A, B, prec=mode)
     Cw = run(A, B, "precise", dtype, comp)
@@ -85,7 +85,7 @@ def test_windows_match_rounds_and_oracle(mode, dtype, comp):
         assert_close_to_gustavson(Cr, R, R, rows)
 
 
-def test_windows_are_taken():
+def test_tiles_are_taken():
     """With long_window the long rows run as the plan (symbolic pass) and one
     tile launch (numeric pass)."""
     R = I.rmat(12, 16, seed=85)
@@ -139,7 +139,7 @@ def test_hot_cells(mode, dtype, comp, ncols):
         assert_close_to_gustavson(C, A, B)
 
 
-def test_windows_degenerate_rows():
+def test_tiles_degenerate_rows():
     """Every list the same one column (one run of 2048 products), 1096 of
     them and 949 lists of five columns of the same cell (a hot tile of 5841
     products), one list of 10000 products, two identical lists, a row of
@@ -161,7 +161,7 @@ def test_windows_degenerate_rows():
     assert_rows_exact(run(A, B, "upper"), ref)
 
 
-def test_windows_wide_B_several_bitmap_windows():
+def test_tiles_wide_B_several_bitmap_windows():
     """B with 3 * 2^20 + 5 columns: the plan takes four bitmap windows (cells
     of 128 columns), some rows have no product in some of them."""
     k, ncols = 3000, 3 * (1 << 20) + 5
@@ -176,7 +176,7 @@ def test_windows_wide_B_several_bitmap_windows():
     assert_rows_exact(run(A2, Bl), oracle.alg1(A2, Bl))
 
 
-def test_windows_list_limit_uses_merge_rounds():
+def test_tiles_list_limit_uses_merge_rounds():
     """Rows of more than 65535 lists keep the merge rounds: alone (one
     symbolic launch, the column bitmap), and mixed with tiled rows in the
     same passes (the plan and the bitmap, the tiles and the rounds)."""
@@ -196,7 +196,7 @@ def test_windows_list_limit_uses_merge_rounds():
     assert sym == 2 and num >= 2
 
 
-def test_windows_batched_and_graph_replay():
+def test_tiles_batched_and_graph_replay():
     """Long rows of two products in one batched call, and a prepared batch
     whose numeric pass (the window kernel among its launches) is replayed
     from a CUDA graph on new values."""
