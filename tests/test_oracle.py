@@ -415,3 +415,33 @@ def test_sampled_rows_match_full():
         c, v = samp.row(t)
         c0, v0 = full.row(int(i))
         assert np.array_equal(c, c0) and np.array_equal(v, v0)
+
+
+def test_balanced_row_groups_brute_force():
+    """Section III-D's static split (reading: group g starts at the first row
+    whose exclusive nprod prefix reaches floor(g * total / p)) against a
+    direct search, and its balance: no group holds more than total / p plus
+    its largest row."""
+    rng = np.random.default_rng(1406)
+    cases = [np.array([5, 5, 5, 5]), np.array([1, 100, 1, 1]), np.zeros(6, np.int64), np.array([7])]
+    cases += [rng.integers(0, 50, size=n) * (rng.random(n) < 0.7) for n in (1, 2, 9, 40, 300)]
+    for nprod in cases:
+        nprod = np.asarray(nprod, np.int64)
+        total = int(nprod.sum())
+        for p in (1, 2, 3, 7, 16):
+            b = oracle.balanced_row_groups(nprod, p)
+            want = [0]
+            for g in range(1, p):
+                target = total * g // p
+                i = 0
+                while i < len(nprod) and int(nprod[:i].sum()) < target:
+                    i += 1
+                want.append(max(i, want[-1]))
+            want.append(len(nprod))
+            assert [int(x) for x in b] == want
+            assert all(x <= y for x, y in zip(b, b[1:]))
+            for g in range(p):
+                part = nprod[b[g]:b[g + 1]]
+                if len(part):
+                    assert int(part.sum()) <= total / p + int(part.max())
+    assert [int(x) for x in oracle.balanced_row_groups(np.array([5, 5, 5, 5]), 2)] == [0, 2, 4]
