@@ -276,7 +276,7 @@ def options(validate=False, compensated=False, warp_max_nprod=0, block_max_nprod
     o.upper_chunk_bytes = upper_chunk_bytes
     if long_window is not None:
         # True: every long row of at most 2048 lists takes the column tiles
-        o.long_window = long_window if type(long_window) is int else (2 if long_window else 0)
+        o.long_window = (2 if long_window else 0) if isinstance(long_window, bool) else int(long_window)
     return o
 
 
